@@ -1,0 +1,440 @@
+"""Benchmark of the time-domain Lienard-Wiechert path on GB300.
+
+One step = one pass of the whole path over the synthetic workload:
+trajectory relayout (lw_trajectories_upload, device-resident FP64 inputs),
+time map + field + interpolated deposit (lw_deposit_time_domain) and the
+per-pixel FFT spectrum (lw_spectrum).  The headline is the mixed path
+(FP64-exact bin coordinates, FP32 field and accumulation); the FP64 path is
+timed beside it and the mixed spectrum is compared with the FP64 one.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) each rank owns its own
+detector (weak scaling, the paper's detector parallelization): no collective
+touches the data path; a barrier and a MAX over ranks bracket the timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LW deposits/s (electron·step·pixel), mixed vs FP64 at ≤1e-4 spectrum error"
+UNIT = "deposits/s"
+WORKLOAD = ("c2_paper: 10,000 electrons (Gaussian bunch 5x5x10 um, gamma 60 +-0.1%, "
+            "eps_n 0.5 mm mrad) x 10,000 Boris steps in a Gaussian laser (0.8 um, a0 0.5, "
+            "w0 20 um, 30 fs) x 64x64 pixels over +-1.5/gamma; 65,536 observer bins")
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in a thread."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel_src):
+    """Per-launch DRAM bytes of the deposit kernel from the committed ncu summary,
+    valid only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "deposit_mixed_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256_16") != _source_hash(kernel_src):
+        return None
+    return d.get("bytes_per_launch_full_size")
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(args, rank):
+    from workloads import configs
+    w = configs.c2_paper(n_e=args.n_e, n_s=args.n_s, nx=args.nx, n_bins=args.n_bins)
+    if rank > 0:
+        # weak scaling: rank r observes its own detector, rotated about the beam axis
+        ang = rank * 2.0 * math.pi / max(args.world, 1) * 0.5
+        c, s = math.cos(ang), math.sin(ang)
+        n = w.n_hat.copy()
+        w.n_hat = np.stack([c * n[:, 0] - s * n[:, 1], s * n[:, 0] + c * n[:, 1], n[:, 2]], -1)
+    return w
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2206_03015_gb300 import lw
+
+    dev = torch.device("cuda", _env_int("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    t_gen = time.time()
+    w = make_workload(args, rank)
+    t_gen = time.time() - t_gen
+    tr = w.traj
+    n_dep = w.deposits
+    # device-resident FP64 inputs
+    t_d = torch.from_numpy(tr.t).to(dev)
+    r_d = torch.from_numpy(tr.r).to(dev)
+    b_d = torch.from_numpy(tr.beta).to(dev)
+    a_d = torch.from_numpy(tr.beta_dot).to(dev)
+    det = lw.Detector(w.n_hat, device=dev)
+    # grid (Eqs. tu_min, tu_max) once; it is fixed for the workload
+    traj0 = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_MIXED,
+                                      block=args.block, device=dev)
+    bnd = lw.lw_grid_bounds(traj0, det).cpu().numpy()
+    grid = lw.grid_from_bounds(bnd[0], bnd[1], w.n_bins)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
+    rec_m = torch.empty(shp, dtype=dt, device=dev)
+    S_m = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float32, device=dev)
+    ws_s = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_MIXED, det.n_pix, grid), dev)
+    ws_t = traj0.ws
+    ev_dep = []
+
+    def step_mixed(timed=False):
+        traj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_MIXED,
+                                         block=args.block, device=dev, ws=ws_t)
+        if timed:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+        lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED, record=rec_m, status=status)
+        if timed:
+            e1.record()
+            ev_dep.append((e0, e1))
+        lw.lw_spectrum(rec_m, lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S_m)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed_loop(fn, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            fn(False)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(steps):
+            fn(True)
+        s1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        ms = s0.elapsed_time(s1)
+        if dist is not None:
+            x = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            ms = float(x.item())
+        return ms, clocks
+
+    sampler = ClockSampler(dev.index)
+    ms_m, clocks = timed_loop(step_mixed, args.steps, args.warmup, sampler)
+    ms_step = ms_m / args.steps
+    dep_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_dep)
+    value = n_dep * world / (ms_step * 1e-3)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.full else f"c2_paper reduced: {args.n_e} e x "
+                   f"{args.n_s} steps x {args.nx}x{args.nx} px, {args.n_bins} bins",
+                   "n_e": tr.n_e, "n_s": tr.n_s, "n_pix": w.n_pix, "n_bins": w.n_bins,
+                   "deposits_per_step_per_gpu": n_dep, "block": args.block,
+                   "l2": "inputs larger than L2 (mixed trajectory section %.1f GB)"
+                         % (traj0.ws.numel() / 1e9),
+                   "parallelism": f"detector-sharded x{world} (one detector per GPU)",
+                   "generation_s": round(t_gen, 1)},
+    }
+    # roofline of the dominant kernel (mixed deposit): ALU bound, FP32 lanes
+    alg_flops_per_dep = 9.0     # 4 FFMA (8 flops) + 1 compare per electron-step-pixel
+    sm_max = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
+    except (OSError, ValueError):
+        pass
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FP32 FMA lanes at max clock
+    achieved = alg_flops_per_dep * n_dep / (dep_ms * 1e-3) / 1e12
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2206_03015_gb300", "csrc",
+                                                 "lw_deposit.cu"))
+    result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
+                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                          "kernel": "deposit_mixed_kernel", "kernel_ms": dep_ms,
+                          "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz "
+                                       "(derived, not measured)" % sm_max}
+    result["clocks"] = clocks
+    torch.cuda.synchronize()
+    st_m = int(status.item())
+
+    # FP64 path beside it (fewer steps: it is ~two orders slower on GB300's FP64 pipe)
+    fp64 = None
+    S_64 = None
+    if not args.no_fp64:
+        del traj0
+        rec_d = torch.empty(lw.record_shape(det, grid, lw.LW_FP64)[0], dtype=torch.float64,
+                            device=dev)
+        S_d = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float64, device=dev)
+        ws_sd = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_FP64, det.n_pix, grid), dev)
+        trajd = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
+                                          device=dev)
+        ws_d = trajd.ws
+
+        def step_fp64(timed=False):
+            tj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
+                                           device=dev, ws=ws_d)
+            lw.lw_deposit_time_domain(tj, det, grid, lw.LW_FP64, record=rec_d, status=status)
+            lw.lw_spectrum(rec_d, lw.LW_FP64, det.n_pix, grid, ws=ws_sd, out=S_d)
+
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        ms_d, _ = timed_loop(step_fp64, k64, 1)
+        fp64 = {"value": n_dep * world / (ms_d / k64 * 1e-3), "ms_per_step": ms_d / k64,
+                "steps": k64, "warmup": 1}
+        S_64 = S_d
+    # accuracy of the mixed spectrum against the FP64 GPU spectrum (parity-tested vs oracle)
+    acc = {}
+    if S_64 is not None:
+        a = S_m.double()
+        b = S_64
+        acc["spectrum_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(a - b) /
+                                                     torch.linalg.norm(b))
+        # per band, on-axis-like fundamental omega_1(theta) +-20% and its 2nd harmonic
+        from workloads.planewave import doppler_fundamental
+        om = grid.omega.to(dev)
+        th2 = torch.from_numpy(w.theta_x**2 + w.theta_y**2).to(dev)
+        w1 = doppler_fundamental(w.gamma, w.lam, w.a0) / (1.0 + (w.gamma**2) * th2 /
+                                                          (1 + 0.5 * w.a0**2))
+        for name, h in (("fundamental", 1.0), ("harmonic2", 2.0)):
+            mask = (om[None, :] > 0.8 * h * w1[:, None]) & (om[None, :] < 1.2 * h * w1[:, None])
+            if bool(mask.any()):
+                acc[f"rel_l2_{name}"] = float(torch.linalg.norm((a - b)[mask]) /
+                                              torch.linalg.norm(b[mask]))
+            else:
+                acc[f"rel_l2_{name}"] = None
+                acc[f"{name}_note"] = "band above Nyquist of this grid (aliased record)"
+    result["fp64"] = fp64
+    result["accuracy"] = acc
+    result["status"] = {"mixed": st_m, "note": "8 = last arrival on grid point n_bins (clipped)"}
+
+    # end to end through the C ABI from pinned host buffers, spectrum read back
+    if not args.no_e2e:
+        h = [torch.from_numpy(x).pin_memory() for x in (tr.t, tr.r, tr.beta, tr.beta_dot)]
+        S_host = torch.empty(S_m.shape, dtype=torch.float32).pin_memory()
+
+        def step_e2e(timed=False):
+            traj = lw.lw_trajectories_upload(*h, sections=lw.LW_SECTION_MIXED, block=args.block,
+                                             device=dev, ws=ws_t)
+            lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED, record=rec_m, status=status)
+            lw.lw_spectrum(rec_m, lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S_m)
+            S_host.copy_(S_m, non_blocking=True)
+
+        ms_e, _ = timed_loop(step_e2e, args.steps, min(args.warmup, 3))
+        h2d = sum(x.numel() * x.element_size() for x in h)
+        result["e2e"] = {"value": n_dep * world / (ms_e / args.steps * 1e-3), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": S_host.numel() * S_host.element_size(),
+                         "ms_per_step": ms_e / args.steps}
+    # launches of our kernels per step: upload (ends, check, build), deposit (1),
+    # spectrum (twiddle, pass1, pass2 | direct)
+    spec_k = 2 if grid.n_bins <= 4096 else 3
+    result["gpu_launches"] = args.steps * (3 + 1 + spec_k)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, grid, S_m, args)
+    return result
+
+
+def cpu_baseline(w, grid, S_gpu, args):
+    """The FP64 oracle (as it stands) on a bounded sample of the same workload:
+    all electrons and steps for a subset of pixels, timed on the host cores."""
+    import oracle
+    tr = w.traj
+    n_threads = oracle.num_threads()
+    # calibrate on one pixel, then size the sample for ~args.cpu_seconds
+    t0 = time.time()
+    oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat[:1], grid.t_min, grid.dt_u,
+                       grid.n_bins)
+    one = max(time.time() - t0, 1e-3)
+    n_pix = int(max(1, min(w.n_pix, args.cpu_seconds / one * n_threads)))
+    n_pix = max(n_threads, (n_pix // n_threads) * n_threads) if n_pix >= n_threads else n_pix
+    idx = np.linspace(0, w.n_pix - 1, n_pix).astype(np.int64)
+    t0 = time.time()
+    rec, _ = oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat[idx], grid.t_min,
+                                grid.dt_u, grid.n_bins)
+    S = oracle.spectrum(rec, grid.dt_u)
+    dt = time.time() - t0
+    dep = tr.n_e * tr.n_s * n_pix
+    S_g = S_gpu[idx.tolist()].double().cpu().numpy()
+    err = float(np.linalg.norm(S_g - S) / np.linalg.norm(S))
+    return {"value": dep / dt, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+            "sample": f"{n_pix} of {w.n_pix} pixels (all {tr.n_e} electrons x {tr.n_s} steps), "
+                      f"deposit + FFT spectrum, {dt:.1f} s",
+            "mixed_spectrum_rel_l2_vs_oracle_on_sample": err}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed as the reference arm: each step is a bounded sample
+    (a subset of pixels, all electrons and steps) of the same workload."""
+    if rank != 0:
+        return None
+    import oracle
+    w = make_workload(args, 0)
+    tr = w.traj
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, w.n_hat)
+    dt_u = (hi - lo) / w.n_bins
+    n_threads = oracle.num_threads()
+    t0 = time.time()
+    oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat[:1], lo, dt_u, w.n_bins)
+    one = max(time.time() - t0, 1e-3)
+    budget = max(1.0, args.ref_seconds / max(1, args.steps + args.warmup))
+    n_pix = int(max(1, min(w.n_pix, budget / one * n_threads)))
+    idx = np.linspace(0, w.n_pix - 1, n_pix).astype(np.int64)
+
+    def step():
+        rec, _ = oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat[idx], lo, dt_u,
+                                    w.n_bins)
+        oracle.spectrum(rec, dt_u)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.time()
+    for _ in range(args.steps):
+        step()
+    dt = (time.time() - t0) / args.steps
+    dep = tr.n_e * tr.n_s * n_pix
+    v = dep / dt
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_pixels_per_step": n_pix},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                             "sample": f"{n_pix} of {w.n_pix} pixels per step, all electrons "
+                                       f"and steps, deposit + FFT"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-e", type=int, default=10_000)
+    ap.add_argument("--n-s", type=int, default=10_000)
+    ap.add_argument("--nx", type=int, default=64)
+    ap.add_argument("--n-bins", type=int, default=65_536)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    args = ap.parse_args()
+    args.full = (args.n_e, args.n_s, args.nx, args.n_bins) == (10_000, 10_000, 64, 65_536)
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    args.world = world
+    dist = None
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as tdist
+        import torch
+        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        tdist.init_process_group(backend="nccl")
+        dist = tdist
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, dist)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * lw.h -- C ABI of liblw.so, a GB300 (sm_103a) implementation of the
+ * time-domain Lienard-Wiechert radiation method of Kan, Kaertner, Le Borne,
+ * Ruprecht, Zemke, "Parallel Computation of Inverse Compton Scattering
+ * Radiation Spectra based on Lienard-Wiechert Potentials" (arXiv 2206.03015).
+ *
+ * Pipeline (one call per stage, all asynchronous on the caller's stream):
+ *   lw_trajectories_upload  stored trajectories -> device layout       (Sec. 4.2, "Beam")
+ *   lw_grid_bounds          t_u^min, t_u^max of the observer grid       (Eqs. tu_min, tu_max)
+ *   lw_deposit_time_domain  advanced times + LW far field + linear
+ *                           interpolation onto the uniform grid         (Eqs. far_adv, far_efield,
+ *                                                                         Algorithm 2)
+ *   lw_spectrum             per-pixel FFT -> d2I/domega dOmega          (Eqs. efield_xfrom,
+ *                                                                         const_phase_drop)
+ *   lw_spectrum_grad        adjoint of deposit + spectrum
+ *
+ * Conventions shared by every entry point:
+ *  - The caller owns all memory.  The library allocates no device or host
+ *    memory; every buffer (including workspaces, sized by a query call) is
+ *    passed in.  Pointers marked "device" must be device memory or memory the
+ *    GPU can address (pinned host memory is accepted wherever a kernel reads
+ *    an input once).
+ *  - Every call enqueues work on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream) and returns without synchronising.
+ *  - Host-detectable argument errors are returned synchronously as a negative
+ *    lw_status and enqueue nothing.  LW_ECUDA reports a failed launch.
+ *  - Data-dependent conditions found by the kernels are OR-ed into the
+ *    caller's device status word (int32, LW_ST_* bits); read it after the
+ *    stream has been synchronised.  Kernels never trap.
+ *  - The library holds no global state; calls on different streams may run
+ *    concurrently as long as they do not write the same buffers.
+ *
+ * Units are SI: t [s], r [m], beta [1], beta_dot [1/s].  Field records hold
+ * the LW far field divided by the constant q/(4 pi eps0 c0 R), i.e.
+ *   F = n x ((n - beta) x beta_dot) / (1 - n.beta)^3       [1/s].
+ */
+#ifndef LW_H
+#define LW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LW_OK = 0,
+    LW_EINVAL = -1,        /* invalid argument (null pointer, bad size, bad flag) */
+    LW_ESIZE = -2,         /* workspace smaller than required */
+    LW_ECUDA = -3,         /* a CUDA launch or runtime call failed */
+    LW_EUNSUPPORTED = -4,  /* valid but unsupported (e.g. n_bins not a power of two for the FFT) */
+    LW_ETIMEOUT = -5       /* a bounded device-side wait ran out */
+} lw_status;
+
+/* Arithmetic of a call. */
+enum {
+    LW_FP64 = 0,   /* everything in FP64; advanced times and bin indices follow the op order
+                      documented at lw_deposit_time_domain (bit-identical to a plain C loop
+                      compiled without FMA contraction) */
+    LW_MIXED = 1,  /* FP64-exact bin coordinates carried as integer + FP32 fraction, FP32
+                      field and interpolation, contributions added to an FP64 record by
+                      the L2 (red.global.add.f64), FP32 FFT */
+    LW_MIXED_KAHAN = 2  /* as LW_MIXED but the record is a compensated FP32 pair
+                           (sum, compensation): atomic add with return + two-sum */
+};
+
+/* Field terms (bit mask) of lw_deposit_time_domain. */
+enum {
+    LW_FIELD_ACCEL = 1,     /* acceleration (radiation) field, Eq. far_efield */
+    LW_FIELD_VELOCITY = 2   /* far-field velocity field c0 (n-beta)(1-beta^2)/((1-n.beta)^3 R) */
+};
+
+/* Device status bits (OR-ed into the caller's int32 status word). */
+enum {
+    LW_ST_BETA = 1,        /* |beta| >= 1 at a sample (its field is taken as 0) */
+    LW_ST_NONFINITE = 2,   /* non-finite input, or a bin coordinate beyond +-2^62 */
+    LW_ST_TIME = 4,        /* lab time not strictly increasing along a trajectory */
+    LW_ST_CLIP = 8,        /* grid points outside [0, n_bins) were skipped */
+    LW_ST_TA_ORDER = 16    /* advanced time not increasing between two samples (LW_FP64) */
+};
+
+/* Which device sections lw_trajectories_upload builds (bit mask). */
+enum { LW_SECTION_FP64 = 1, LW_SECTION_MIXED = 2 };
+
+/* Stored trajectories as given by the caller (all float64, C order).
+ *   t         [n_s+1] shared by all electrons, or [n_e][n_s+1] if t_per_electron
+ *   r         [n_e][n_s+1][3]   position
+ *   beta      [n_e][n_s+1][3]   velocity / c0
+ *   beta_dot  [n_e][n_s+1][3]   d beta / dt
+ * Pointers are device or pinned-host memory; they are read once by
+ * lw_trajectories_upload and not referenced afterwards. */
+typedef struct {
+    int64_t n_e;
+    int64_t n_s;
+    const double* t;
+    int32_t t_per_electron;
+    const double* r;
+    const double* beta;
+    const double* beta_dot;
+} lw_traj_in;
+
+/* Device view of uploaded trajectories (plain old data; all pointers point
+ * into the workspace passed to lw_trajectories_upload, which the caller must
+ * keep alive and unmodified while the view is used). */
+typedef struct {
+    int64_t n_e, n_s;
+    int32_t t_per_electron;
+    int32_t sections;       /* LW_SECTION_* bits that were built */
+    int32_t block;          /* samples per anchoring block of the mixed section */
+    int32_t n_blocks;       /* ceil((n_s+1) / block) */
+    const double* t;        /* FP64 section: copies of the inputs (same layouts) */
+    const double* r;
+    const double* beta;
+    const double* beta_dot;
+    const void* scan;       /* MIXED: float4 [n_e][n_s+1] (tau - tau_b, r - r_b) per sample,
+                               tau = t - z/c0, _b = first sample of the sample's block */
+    const void* field;      /* MIXED: float [n_e][n_s+1][6] (beta_x, beta_y, 1 - beta_z,
+                               beta_dot_x, beta_dot_y, beta_dot_z) */
+    const double* anchor;   /* MIXED: double4 [n_e][n_blocks] (tau_b, x_b, y_b, z_b) */
+    const double* ends;     /* always: double [n_e][2][4] = (t, x, y, z) of the first and
+                               the last sample of each electron */
+    const int32_t* input_status; /* device int32: LW_ST_* found while uploading */
+} lw_traj;
+
+/* Far-field detector: n_pix unit directions n_hat [n_pix][3] (float64, device) on a
+ * sphere of radius R (used only by LW_FIELD_VELOCITY). */
+typedef struct {
+    int64_t n_pix;
+    const double* n_hat;
+    double R;
+} lw_detector;
+
+/* Uniform observer grid t_j = t_min + j * dt_u, j = 0 .. n_bins-1. */
+typedef struct {
+    double t_min;
+    double dt_u;
+    int64_t n_bins;
+} lw_grid;
+
+/* Copy stored trajectories into the device layout of `ws` (Sec. 4.2 "Beam":
+ * position, velocity and acceleration per particle; here for every step).
+ *   sections   LW_SECTION_FP64 and/or LW_SECTION_MIXED
+ *   block      samples per anchoring block of the mixed section (16..1024,
+ *              power of two; 0 = default 128)
+ *   ws         device workspace, 256-byte aligned; NULL = size query
+ *   ws_bytes   in: size of ws; out: bytes required
+ *   out        filled with the device view on success
+ * Checks every sample (finite values, |beta| < 1, strictly increasing t) and
+ * records LW_ST_* bits in the workspace for later deposits.
+ * Errors: LW_EINVAL (null in/out pointers, n_e < 1, n_s < 1, bad sections or
+ * block), LW_ESIZE (ws too small; *ws_bytes = required), LW_ECUDA. */
+int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, int32_t block, void* ws,
+                           size_t* ws_bytes, lw_traj* out, void* stream);
+
+/* Observer-grid bounds, Eqs. (tu_min) and (tu_max):
+ *   bounds[0] = min over (k, m) of t_a^{k,m}(t_start),
+ *   bounds[1] = max over (k, m) of t_a^{k,m}(t_end),
+ * with the FP64 advanced time of lw_deposit_time_domain (constant |x|/c0
+ * dropped).  bounds: device double[2].  Works with either section.
+ * Errors: LW_EINVAL, LW_ECUDA. */
+int lw_grid_bounds(const lw_traj* traj, const lw_detector* det, double* bounds, void* stream);
+
+/* Time-domain method, Algorithm 2, for every pixel of the detector.
+ * For each electron k, pixel m and step i the advanced time (Eq. far_adv,
+ * without the constant |x|/c0) and bin coordinate are
+ *   t_a = t_i - (n . r_i) * (1/c0),   u = (t_a - t_min) * (1/dt_u),
+ * and every grid point j with floor(u_{i-1}) < j <= floor(u_i) (the
+ * half-open interval (t_b, t_a] of Algorithm 2) receives
+ *   F_{i-1} (t_a - t_j)/(t_a - t_b) + F_i (t_j - t_b)/(t_a - t_b).
+ * LW_FP64 evaluates n.r as ((n_x x + n_y y) + n_z z) and every operation
+ * above in that order with single IEEE roundings.  LW_MIXED evaluates u as
+ * an integer plus an FP32 fraction anchored once per block in
+ * double-FP32 arithmetic (the first and last samples' bins in FP64, as in
+ * LW_FP64), the field in FP32 from the stable form
+ *   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
+ *   F = [(n - beta)(n . beta_dot) - D beta_dot] / D^3,
+ * and accumulates into FP64 (LW_MIXED) or compensated FP32 pairs (LW_MIXED_KAHAN).
+ *   precision    LW_FP64, LW_MIXED or LW_MIXED_KAHAN (the matching section must exist)
+ *   field_flags  LW_FIELD_* mask (non-zero)
+ *   record       device, 8 bytes per value; LW_FP64 and LW_MIXED: double
+ *                [n_pix][3][n_bins]; LW_MIXED_KAHAN: float2 [n_pix][3][n_bins] =
+ *                (sum, compensation), value = sum + compensation
+ *   accumulate   0: the record is zeroed first; 1: add to its contents
+ *   status       device int32, OR-ed with LW_ST_* bits (may be NULL)
+ * Grid points outside [0, n_bins) are skipped (LW_ST_CLIP).
+ * Errors: LW_EINVAL (null pointers, n_bins < 1, dt_u <= 0 or non-finite,
+ * missing section, zero flags), LW_ECUDA. */
+int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* det, const lw_grid* grid,
+                           int32_t precision, uint32_t field_flags, void* record,
+                           int32_t accumulate, int32_t* status, void* stream);
+
+/* Spectral-angular distribution from the records (Eq. efield_xfrom and the
+ * prefactor of Eq. const_phase_drop):
+ *   S[m][l] = q^2 dt_u^2 / (16 pi^3 eps0 c0) * sum_c |X_{m,c}(l)|^2,
+ *   X_{m,c}(l) = sum_j rec[m][c][j] exp(+2 pi i j l / n_bins),  l = 0 .. n_bins/2,
+ * at omega_l = 2 pi l / (n_bins dt_u), in J s / sr (per unit angular frequency).
+ *   record    device, layout of lw_deposit_time_domain for `precision`
+ *   n_pix     pixels in the record
+ *   q         particle charge [C]
+ *   spectrum  device; LW_FP64: double, LW_MIXED(_KAHAN): float [n_pix][n_bins/2+1]
+ *   X_save    device or NULL; receives X' = sqrt(K) dt_u X (so that S = sum_c |X'_c|^2),
+ *             K = q^2/(16 pi^3 eps0 c0), as LW_FP64: double2, LW_MIXED(_KAHAN): float2
+ *             [n_pix][3][n_bins/2+1]
+ *   ws        device scratch for the two-pass FFT (n_bins above 4096); NULL = query
+ *   ws_bytes  in: size of ws; out: bytes required (0 when none is needed)
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (n_bins not a power of two in
+ * [2, 2^18]), LW_ESIZE, LW_ECUDA. */
+int lw_spectrum(const void* record, int32_t precision, int64_t n_pix, const lw_grid* grid,
+                double q, void* spectrum, void* X_save, void* ws, size_t* ws_bytes,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LW_H */

@@ -1,0 +1,566 @@
+// Time-domain deposit (Algorithm 2 of the paper) for every pixel.
+//
+// Thread mapping (both precisions): one thread owns one (mixed: PIX) detector
+// pixel(s) -- the paper's "detector parallelization" on one GPU -- and a CTA
+// walks a chunk of electrons; the samples of the current electron are staged
+// in shared memory once per CTA and read by all of its pixels as broadcasts.
+// Each step costs the time map and one compare; the field (Eq. far_efield)
+// and the interpolation weights are evaluated only when the step's interval
+// (t_b, t_a] contains grid points, and those contributions are added to the
+// record with global atomics (pixels of different CTAs share bins through
+// electrons of other chunks).
+//
+// FP64 path: every operation of the time map, the bin index, the field and
+// the weights is written with explicit round-to-nearest intrinsics in the
+// order documented in lw.h, so advanced times, bin indices and per-sample
+// contributions are bit-identical to a plain C loop without FMA contraction;
+// only the order of the atomic additions differs.
+//
+// Mixed path: the bin coordinate u = (t_a - t_min)/dt_u is anchored once per
+// block of samples in double-FP32 arithmetic (integer part + FP32 fraction)
+// and advanced per sample with four FP32 FMAs of small, block-relative
+// quantities; the field is FP32 in the stable form
+//   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
+// and contributions are added with a compensated pair of FP32 atomics.
+#include <math.h>
+
+#include "lw_internal.cuh"
+
+namespace lw {
+namespace {
+
+struct DepositArgs {
+    int64_t n_e, ns1;
+    int t_per_e;
+    const double* t;
+    const double* r;
+    const double* beta;
+    const double* bdot;
+    const float4* scan;
+    const float* field;
+    const D4* anchor;
+    int block, n_blocks;
+    const int32_t* input_status;
+    const double* ends;
+    const double* n_hat;
+    int64_t n_pix;
+    double R;
+    double t_min, dt_u, inv_dtu;
+    int64_t n_bins;
+    uint32_t flags;
+    void* record;
+    int32_t* status;
+    int e_chunk;
+};
+
+// ------------------------------------------------------------------ FP64
+
+constexpr int kFp64Threads = 128;
+constexpr int kFp64Tile = 64;
+
+// Field of one sample with the oracle's operation order (see lw.h).
+__device__ int field_fp64(double nx, double ny, double nz, double R, uint32_t flags,
+                          const double* __restrict__ b, const double* __restrict__ a,
+                          double F[3]) {
+    F[0] = F[1] = F[2] = 0.0;
+    const double b0 = b[0], b1 = b[1], b2v = b[2];
+    const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
+                                __dmul_rn(b2v, b2v));
+    const double nb = __dadd_rn(__dadd_rn(__dmul_rn(nx, b0), __dmul_rn(ny, b1)),
+                                __dmul_rn(nz, b2v));
+    const double D = __dsub_rn(1.0, nb);
+    if (!(bb < 1.0) || !(D > 0.0)) return LW_ST_BETA;
+    const double D3 = __dmul_rn(__dmul_rn(D, D), D);
+    const double m0 = __dsub_rn(nx, b0), m1 = __dsub_rn(ny, b1), m2 = __dsub_rn(nz, b2v);
+    if (flags & LW_FIELD_ACCEL) {
+        const double a0 = a[0], a1 = a[1], a2 = a[2];
+        // inner = (n - beta) x beta_dot
+        const double i0 = __dsub_rn(__dmul_rn(m1, a2), __dmul_rn(m2, a1));
+        const double i1 = __dsub_rn(__dmul_rn(m2, a0), __dmul_rn(m0, a2));
+        const double i2 = __dsub_rn(__dmul_rn(m0, a1), __dmul_rn(m1, a0));
+        // outer = n x inner
+        const double o0 = __dsub_rn(__dmul_rn(ny, i2), __dmul_rn(nz, i1));
+        const double o1 = __dsub_rn(__dmul_rn(nz, i0), __dmul_rn(nx, i2));
+        const double o2 = __dsub_rn(__dmul_rn(nx, i1), __dmul_rn(ny, i0));
+        F[0] = __ddiv_rn(o0, D3);
+        F[1] = __ddiv_rn(o1, D3);
+        F[2] = __ddiv_rn(o2, D3);
+    }
+    if (flags & LW_FIELD_VELOCITY) {
+        const double g = __ddiv_rn(__dmul_rn(kC0, __dsub_rn(1.0, bb)), __dmul_rn(D3, R));
+        F[0] = __dadd_rn(F[0], __dmul_rn(m0, g));
+        F[1] = __dadd_rn(F[1], __dmul_rn(m1, g));
+        F[2] = __dadd_rn(F[2], __dmul_rn(m2, g));
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(kFp64Threads) deposit_fp64_kernel(DepositArgs p) {
+    __shared__ double s_t[kFp64Tile];
+    __shared__ double s_r[kFp64Tile * 3];
+    const int64_t m = (int64_t)blockIdx.x * kFp64Threads + threadIdx.x;
+    const bool active = m < p.n_pix;
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    if (active) {
+        nx = p.n_hat[3 * m];
+        ny = p.n_hat[3 * m + 1];
+        nz = p.n_hat[3 * m + 2];
+    }
+    double* rec = static_cast<double*>(p.record) + (active ? m * 3 * p.n_bins : 0);
+    int bits = 0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.input_status)
+        bits |= *p.input_status;
+    const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
+    const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
+    for (int64_t k = k0; k < k1; ++k) {
+        const double* tk = p.t + (p.t_per_e ? k * p.ns1 : 0);
+        const double* rk = p.r + 3 * k * p.ns1;
+        const double* bk = p.beta + 3 * k * p.ns1;
+        const double* ak = p.bdot + 3 * k * p.ns1;
+        double tb = 0.0, ub = 0.0;
+        bool ok_b = false;
+        double Fb[3] = {0.0, 0.0, 0.0};
+        int64_t fb_step = -1;
+        for (int64_t i0 = 0; i0 < p.ns1; i0 += kFp64Tile) {
+            const int n = (int)min((int64_t)kFp64Tile, p.ns1 - i0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += kFp64Threads) {
+                s_t[q] = tk[i0 + q];
+                s_r[3 * q] = rk[3 * (i0 + q)];
+                s_r[3 * q + 1] = rk[3 * (i0 + q) + 1];
+                s_r[3 * q + 2] = rk[3 * (i0 + q) + 2];
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int q = 0; q < n; ++q) {
+                const int64_t i = i0 + q;
+                const double ta =
+                    advanced_time_fp64(nx, ny, nz, s_r[3 * q], s_r[3 * q + 1], s_r[3 * q + 2],
+                                       s_t[q]);
+                const double ua = __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
+                const bool ok_a = fabs(ua) < 4.0e18;
+                if (i > 0) {
+                    if (!ok_a || !ok_b) {
+                        bits |= LW_ST_NONFINITE;
+                    } else {
+                        const int64_t j_hi = (int64_t)floor(ua);
+                        const int64_t j_lo = (int64_t)floor(ub) + 1;
+                        if (!(ta > tb)) bits |= LW_ST_TA_ORDER;
+                        if (j_lo <= j_hi) {
+                            int64_t ja = j_lo, jz = j_hi;
+                            if (ja < 0) {
+                                ja = 0;
+                                bits |= LW_ST_CLIP;
+                            }
+                            if (jz > p.n_bins - 1) {
+                                jz = p.n_bins - 1;
+                                bits |= LW_ST_CLIP;
+                            }
+                            if (ja <= jz) {
+                                if (fb_step != i - 1)
+                                    field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * (i - 1),
+                                               ak + 3 * (i - 1), Fb);
+                                double Fa[3];
+                                field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * i, ak + 3 * i, Fa);
+                                const double den = __dsub_rn(ta, tb);
+                                for (int64_t j = ja; j <= jz; ++j) {
+                                    const double tu =
+                                        __dadd_rn(p.t_min, __dmul_rn((double)j, p.dt_u));
+                                    const double wa = __ddiv_rn(__dsub_rn(ta, tu), den);
+                                    const double wb = __ddiv_rn(__dsub_rn(tu, tb), den);
+                                    for (int c = 0; c < 3; ++c)
+                                        atomicAdd(rec + c * p.n_bins + j,
+                                                  __dadd_rn(__dmul_rn(Fb[c], wa),
+                                                            __dmul_rn(Fa[c], wb)));
+                                }
+                                Fb[0] = Fa[0];
+                                Fb[1] = Fa[1];
+                                Fb[2] = Fa[2];
+                                fb_step = i;
+                            }
+                        }
+                    }
+                }
+                tb = ta;
+                ub = ua;
+                ok_b = ok_a;
+            }
+        }
+    }
+    block_status_or(p.status, bits);
+}
+
+// ------------------------------------------------------------------ mixed
+
+constexpr int kMixThreads = 128;
+
+struct DF {   // unevaluated sum hi + lo of two floats
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF split_double(double x) {
+    DF r;
+    r.hi = __double2float_rn(x);
+    r.lo = __double2float_rn(x - (double)r.hi);
+    return r;
+}
+
+// Compensated atomic accumulation into a (sum, compensation) pair: the
+// rounding error of the atomic add is recovered exactly from the returned old
+// value (two-sum) and added to the compensation word.
+__device__ __forceinline__ void kahan_atomic_add(float2* p, float v) {
+    const float old = atomicAdd(&p->x, v);
+    const float s = __fadd_rn(old, v);
+    const float bb = __fsub_rn(s, old);
+    const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    if (err != 0.0f) atomicAdd(&p->y, err);
+}
+
+struct PixelConst {
+    float nx, ny, nz, omnz;   // direction and 1 - n_z (stable)
+};
+
+// Per-sample FP32 field in the stable form (zero if D <= 0).
+__device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __restrict__ f,
+                                           uint32_t flags, float c0_over_R, float F[3]) {
+    const float bx = f[0], by = f[1], eps = f[2];
+    const float ax = f[3], ay = f[4], az = f[5];
+    const float D = fmaf(-pc.ny, by, fmaf(-pc.nx, bx, fmaf(pc.nz, eps, pc.omnz)));
+    F[0] = F[1] = F[2] = 0.0f;
+    if (!(D > 0.0f)) return;
+    const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
+    const float invD = 1.0f / D;
+    const float invD3 = invD * invD * invD;
+    if (flags & LW_FIELD_ACCEL) {
+        const float na = fmaf(pc.nz, az, fmaf(pc.ny, ay, pc.nx * ax));
+        F[0] = fmaf(mx, na, -D * ax) * invD3;
+        F[1] = fmaf(my, na, -D * ay) * invD3;
+        F[2] = fmaf(mz, na, -D * az) * invD3;
+    }
+    if (flags & LW_FIELD_VELOCITY) {
+        const float g2 = fmaf(-by, by, fmaf(-bx, bx, eps * (2.0f - eps)));   // 1 - beta^2
+        const float g = c0_over_R * g2 * invD3;
+        F[0] = fmaf(mx, g, F[0]);
+        F[1] = fmaf(my, g, F[1]);
+        F[2] = fmaf(mz, g, F[2]);
+    }
+}
+
+// A step whose interval (t_b, t_a] contains grid points, recorded by the scan
+// loop of one lane and deposited later by the whole warp.
+struct Event {
+    int slot;     // lane * PIX + q: pixel of the warp
+    int qq;       // step index within the staged block (sample i0 + qq)
+    int ja;       // first grid point (clipped)
+    int cnt;      // number of grid points
+    float a0;     // ja - u_{i-1}   [bins]
+    float du;     // u_i - u_{i-1}  [bins]
+};
+
+constexpr int kLaneQ = 8;                       // events per lane between drains
+constexpr int kWarps = kMixThreads / 32;
+
+template <bool KAHAN>
+__device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
+    if (KAHAN) {
+        kahan_atomic_add(static_cast<float2*>(rec) + idx, v);
+    } else {
+        atomicAdd(static_cast<double*>(rec) + idx, (double)v);   // red.global.add.f64
+    }
+}
+
+// FP64 bin index of a trajectory end sample, with the FP64 path's operation order.
+__device__ __forceinline__ int exact_bin(const double* e, double nx, double ny, double nz,
+                                         double t_min, double inv_dtu) {
+    const double ta = advanced_time_fp64(nx, ny, nz, e[1], e[2], e[3], e[0]);
+    double u = __dmul_rn(__dsub_rn(ta, t_min), inv_dtu);
+    u = fmin(fmax(u, -1.0e9), 1.0e9);
+    return (int)floor(u);
+}
+
+template <int PIX, bool KAHAN>
+__global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs p) {
+    extern __shared__ float4 smem4[];
+    const int B = p.block;
+    float4* s_scan = smem4;                                    // [B]
+    float* s_field = reinterpret_cast<float*>(smem4 + B);      // [B+1][6], sample i0-1 first
+    __shared__ float s_anch[8];                                // T, R_x, R_y, R_z (hi, lo)
+    __shared__ Event s_q[kWarps][kLaneQ * 32];                 // [warp][lane * kLaneQ + e]
+    __shared__ int s_qn[kWarps][32];
+    __shared__ PixelConst s_pc[kMixThreads * PIX];
+    __shared__ int64_t s_pix[kMixThreads * PIX];
+    __shared__ float s_wl[kMixThreads * PIX][3];               // lo parts of the slopes
+    __shared__ int s_jlast[kMixThreads * PIX];                 // exact bin of the last sample
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wslot = warp * 32 * PIX;
+    const float s32 = (float)p.inv_dtu;
+    const float c0_over_R = (float)(kC0 / p.R);
+    const int nb = (int)p.n_bins;
+    float wh[PIX][3];
+    bool act[PIX];
+    for (int q = 0; q < PIX; ++q) {
+        const int64_t m = (int64_t)blockIdx.x * kMixThreads * PIX + q * kMixThreads + threadIdx.x;
+        act[q] = m < p.n_pix;
+        double nx = 0.0, ny = 0.0, nz = 1.0;
+        if (act[q]) {
+            nx = p.n_hat[3 * m];
+            ny = p.n_hat[3 * m + 1];
+            nz = p.n_hat[3 * m + 2];
+        }
+        const double omnz = (nx * nx + ny * ny) / (1.0 + nz);   // 1 - n_z without cancellation
+        const double sc = kInvC0 * p.inv_dtu;
+        const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
+        const DF wz = split_double(omnz * sc);
+        wh[q][0] = wx.hi;
+        wh[q][1] = wy.hi;
+        wh[q][2] = wz.hi;
+        const int slot = wslot + lane * PIX + q;
+        s_wl[slot][0] = wx.lo;
+        s_wl[slot][1] = wy.lo;
+        s_wl[slot][2] = wz.lo;
+        s_pc[slot] = PixelConst{(float)nx, (float)ny, (float)nz, (float)omnz};
+        s_pix[slot] = act[q] ? m : 0;
+    }
+    Event* myq = s_q[warp] + lane * kLaneQ;
+    int* qn = s_qn[warp];
+    int nq = 0;                                  // this lane's queued events
+    int bits = 0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.input_status)
+        bits |= *p.input_status;
+
+    const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
+    const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
+    for (int64_t k = k0; k < k1; ++k) {
+        const float4* sck = p.scan + k * p.ns1;
+        const float* fdk = p.field + 6 * k * p.ns1;
+        const D4* anc = p.anchor + k * p.n_blocks;
+        const double* ends = p.ends + 8 * k;
+        // per pixel: I = integer anchor of the block, thr = floor(u_{i-1}) + 1 - I (the
+        // next grid point relative to the anchor), vprev = u_{i-1} - I, f = U_b - I
+        int I[PIX];
+        float vprev[PIX], thr[PIX], f[PIX];
+        for (int q = 0; q < PIX; ++q) {
+            // exact bins of the first and last samples: the half-open interval of
+            // Algorithm 2 makes these the only samples where a one-bin rounding flip
+            // changes the record by a whole sample
+            const int64_t m = s_pix[wslot + lane * PIX + q];
+            const double nx = p.n_hat[3 * m], ny = p.n_hat[3 * m + 1], nz = p.n_hat[3 * m + 2];
+            thr[q] = (float)(exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu) + 1);
+            s_jlast[wslot + lane * PIX + q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
+            I[q] = 0;
+            vprev[q] = 0.0f;
+        }
+        for (int b = 0; b < p.n_blocks; ++b) {
+            const int64_t i0 = (int64_t)b * B;
+            const int n = (int)min((int64_t)B, p.ns1 - i0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += kMixThreads) s_scan[q] = sck[i0 + q];
+            for (int q = threadIdx.x; q < 6 * (n + 1); q += kMixThreads) {
+                const int64_t idx = 6 * (i0 - 1) + q;
+                s_field[q] = (idx >= 0) ? fdk[idx] : 0.0f;
+            }
+            if (threadIdx.x == 0) {
+                const D4 a = anc[b];
+                const DF T = split_double((a.x - p.t_min) * p.inv_dtu);
+                const DF X = split_double(a.y), Y = split_double(a.z), Z = split_double(a.w);
+                s_anch[0] = T.hi;
+                s_anch[1] = T.lo;
+                s_anch[2] = X.hi;
+                s_anch[3] = X.lo;
+                s_anch[4] = Y.hi;
+                s_anch[5] = Y.lo;
+                s_anch[6] = Z.hi;
+                s_anch[7] = Z.lo;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < PIX; ++q) {
+                // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
+                const float* wlq = s_wl[wslot + lane * PIX + q];
+                float s = s_anch[0], e = s_anch[1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float Rh = s_anch[2 + 2 * c], Rl = s_anch[3 + 2 * c];
+                    const float pr = __fmul_rn(wh[q][c], Rh);
+                    float pe = fmaf(wh[q][c], Rh, -pr);
+                    pe = fmaf(wh[q][c], Rl, fmaf(wlq[c], Rh, pe));
+                    const float s2 = __fadd_rn(s, pr);
+                    const float bb = __fsub_rn(s2, s);
+                    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)),
+                                                __fsub_rn(pr, bb));
+                    s = s2;
+                    e = __fadd_rn(e, __fadd_rn(err, pe));
+                }
+                s = fminf(fmaxf(s, -1.0e9f), 1.0e9f);
+                const float Is = floorf(s);
+                const int Inew = (int)Is;
+                f[q] = __fadd_rn(__fsub_rn(s, Is), e);
+                vprev[q] = __fadd_rn(vprev[q], (float)(I[q] - Inew));   // rebase sample i-1
+                thr[q] = act[q] ? thr[q] + (float)(I[q] - Inew) : INFINITY;
+                I[q] = Inew;
+            }
+            int qq = 0;
+            if (b == 0) {   // the first sample only fills the buffer of Algorithm 2
+                const float4 sc = s_scan[0];
+#pragma unroll
+                for (int q = 0; q < PIX; ++q)
+                    vprev[q] = fmaf(wh[q][2], sc.w,
+                                    fmaf(wh[q][1], sc.z, fmaf(wh[q][0], sc.y,
+                                                              fmaf(s32, sc.x, f[q]))));
+                qq = 1;
+            }
+            const bool last_block = (i0 + n == p.ns1);
+            while (true) {
+                // scan until the block ends or some lane's queue could overflow
+                for (; qq < n; ++qq) {
+                    if (__any_sync(0xffffffffu, nq > kLaneQ - PIX)) break;
+                    const float4 sc = s_scan[qq];
+                    const bool is_last = last_block && qq == n - 1;
+#pragma unroll
+                    for (int q = 0; q < PIX; ++q) {
+                        const float v = fmaf(wh[q][2], sc.w,
+                                             fmaf(wh[q][1], sc.z,
+                                                  fmaf(wh[q][0], sc.y, fmaf(s32, sc.x, f[q]))));
+                        bool cross = v >= thr[q];
+                        int jnew = 0;
+                        if (is_last) {   // exact bin of the last sample
+                            jnew = s_jlast[wslot + lane * PIX + q];
+                            cross = act[q] && jnew + 1 - I[q] > (int)thr[q];
+                        }
+                        if (cross) {
+                            if (!is_last) jnew = I[q] + (int)floorf(v);
+                            int ja = (int)thr[q] + I[q], jz = jnew;
+                            if (ja < 0) {
+                                ja = 0;
+                                bits |= LW_ST_CLIP;
+                            }
+                            if (jz > nb - 1) {
+                                jz = nb - 1;
+                                bits |= LW_ST_CLIP;
+                            }
+                            if (ja <= jz) {
+                                Event ev;
+                                ev.slot = lane * PIX + q;
+                                ev.qq = qq;
+                                ev.ja = ja;
+                                ev.cnt = jz - ja + 1;
+                                ev.a0 = __fsub_rn((float)(ja - I[q]), vprev[q]);
+                                ev.du = __fsub_rn(v, vprev[q]);
+                                myq[nq++] = ev;
+                            }
+                            thr[q] = (float)(jnew + 1 - I[q]);
+                        }
+                        vprev[q] = v;
+                    }
+                }
+                // deposit the queued events with all lanes of the warp
+                qn[lane] = nq;
+                __syncwarp();
+                for (int e = lane; e < 32 * kLaneQ; e += 32) {
+                    const int owner = e / kLaneQ, idx = e % kLaneQ;
+                    if (idx >= qn[owner]) continue;
+                    const Event ev = s_q[warp][owner * kLaneQ + idx];
+                    const PixelConst pc = s_pc[wslot + ev.slot];
+                    const int64_t base = s_pix[wslot + ev.slot] * 3 * p.n_bins;
+                    float Fb[3], Fa[3];
+                    field_fp32(pc, s_field + 6 * ev.qq, p.flags, c0_over_R, Fb);
+                    field_fp32(pc, s_field + 6 * (ev.qq + 1), p.flags, c0_over_R, Fa);
+                    const float inv_du = ev.du > 0.0f ? 1.0f / ev.du : 0.0f;
+                    for (int t = 0; t < ev.cnt; ++t) {
+                        const float wb = (ev.a0 + (float)t) * inv_du;
+                        const float wa = 1.0f - wb;
+                        const int64_t j = base + ev.ja + t;
+                        accumulate<KAHAN>(p.record, j, fmaf(Fb[0], wa, Fa[0] * wb));
+                        accumulate<KAHAN>(p.record, j + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+                        accumulate<KAHAN>(p.record, j + 2 * p.n_bins,
+                                          fmaf(Fb[2], wa, Fa[2] * wb));
+                    }
+                }
+                __syncwarp();
+                nq = 0;
+                if (qq >= n) break;
+            }
+        }
+    }
+    block_status_or(p.status, bits);
+}
+
+int pick_chunk(int64_t n_e, int64_t tiles) {
+    // aim for >= 16 resident-CTA waves worth of CTAs over the 152 SMs
+    const int64_t target = (int64_t)kSms * 16;
+    int64_t chunk = (n_e * tiles + target - 1) / target;
+    if (chunk < 1) chunk = 1;
+    if (chunk > n_e) chunk = n_e;
+    return (int)chunk;
+}
+
+}  // namespace
+}  // namespace lw
+
+using namespace lw;
+
+extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* det,
+                                      const lw_grid* grid, int32_t precision,
+                                      uint32_t field_flags, void* record, int32_t accumulate,
+                                      int32_t* status, void* stream) {
+    if (!traj || !det || !grid || !record || !det->n_hat) return LW_EINVAL;
+    if (det->n_pix < 1 || grid->n_bins < 1 || grid->n_bins > (int64_t(1) << 30)) return LW_EINVAL;
+    if (!(grid->dt_u > 0.0) || !isfinite(grid->dt_u) || !isfinite(grid->t_min)) return LW_EINVAL;
+    if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
+    if ((field_flags & LW_FIELD_VELOCITY) && !(det->R > 0.0)) return LW_EINVAL;
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+        return LW_EINVAL;
+    if (precision == LW_FP64 && !(traj->sections & LW_SECTION_FP64)) return LW_EINVAL;
+    if (precision != LW_FP64 && !(traj->sections & LW_SECTION_MIXED)) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const size_t elem = 8;   // double, or a (sum, compensation) float pair
+    if (!accumulate &&
+        cudaMemsetAsync(record, 0, elem * 3 * (size_t)(det->n_pix * grid->n_bins), st) !=
+            cudaSuccess)
+        return LW_ECUDA;
+
+    DepositArgs a{};
+    a.n_e = traj->n_e;
+    a.ns1 = traj->n_s + 1;
+    a.t_per_e = traj->t_per_electron;
+    a.t = traj->t;
+    a.r = traj->r;
+    a.beta = traj->beta;
+    a.bdot = traj->beta_dot;
+    a.scan = static_cast<const float4*>(traj->scan);
+    a.field = static_cast<const float*>(traj->field);
+    a.anchor = reinterpret_cast<const D4*>(traj->anchor);
+    a.block = traj->block;
+    a.n_blocks = traj->n_blocks;
+    a.input_status = traj->input_status;
+    a.ends = traj->ends;
+    a.n_hat = det->n_hat;
+    a.n_pix = det->n_pix;
+    a.R = det->R > 0.0 ? det->R : 1.0;
+    a.t_min = grid->t_min;
+    a.dt_u = grid->dt_u;
+    a.inv_dtu = 1.0 / grid->dt_u;
+    a.n_bins = grid->n_bins;
+    a.flags = field_flags;
+    a.record = record;
+    a.status = status;
+
+    if (precision == LW_FP64) {
+        const int64_t tiles = (det->n_pix + kFp64Threads - 1) / kFp64Threads;
+        a.e_chunk = pick_chunk(traj->n_e, tiles);
+        dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
+        deposit_fp64_kernel<<<g, kFp64Threads, 0, st>>>(a);
+        return launch_status();
+    }
+    constexpr int PIX = 4;
+    const int64_t tiles = (det->n_pix + kMixThreads * PIX - 1) / (kMixThreads * PIX);
+    a.e_chunk = pick_chunk(traj->n_e, tiles);
+    dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
+    const size_t smem = sizeof(float4) * traj->block + sizeof(float) * 6 * (traj->block + 1);
+    if (precision == LW_MIXED_KAHAN)
+        deposit_mixed_kernel<PIX, true><<<g, kMixThreads, smem, st>>>(a);
+    else
+        deposit_mixed_kernel<PIX, false><<<g, kMixThreads, smem, st>>>(a);
+    return launch_status();
+}

@@ -1,0 +1,360 @@
+// Per-pixel spectra from the time records (Eq. efield_xfrom with the
+// prefactor of Eq. const_phase_drop):
+//   S[m][l] = sum_c |X'_{m,c}(l)|^2,  X' = sqrt(K) dt_u X,  K = q^2/(16 pi^3 eps0 c0),
+//   X_{m,c}(l) = sum_j rec[m][c][j] exp(+2 pi i j l / N),  l = 0..N/2.
+//
+// Two real rows are transformed together as one complex sequence
+// z = a + i b; with Z = FFT(z):
+//   A(l) = (Z_l + conj Z_{N-l}) / 2,   B(l) = (Z_l - conj Z_{N-l}) / (2i).
+// A pixel pair (m0, m1) gives three sequences: (x0 + i y0), (x1 + i y1),
+// (z0 + i z1).  Transforms are radix-2 in shared memory with twiddles read
+// from a table e^{+2 pi i t/N} built once per call:
+//   N <= 4096   one CTA per pixel pair, all three sequences in turn;
+//   N >  4096   four-step: N = N1 * N2, pass 1 transforms the N2 columns of
+//               length N1 (coalesced column tiles) and applies the twiddles
+//               e^{2 pi i j2 l1 / N}, pass 2 transforms each row l1 together
+//               with its mirror row N1 - l1, which holds the Z_{N-l} needed by
+//               the split above.
+#include <math.h>
+
+#include "lw_internal.cuh"
+
+namespace lw {
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) {
+    C r;
+    r.x = a.x + b.x;
+    r.y = a.y + b.y;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C csub(C a, C b) {
+    C r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    return r;
+}
+
+__device__ __forceinline__ unsigned bitrev(unsigned x, int bits) {
+    return __brev(x) >> (32 - bits);
+}
+
+// twiddle table tw[t] = exp(+2 pi i t / N), t = 0..N-1, evaluated in FP64
+template <typename T>
+__global__ void twiddle_kernel(typename V2<T>::type* tw, int64_t N) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)N, &s, &c);
+        typename V2<T>::type w;
+        w.x = (T)c;
+        w.y = (T)s;
+        tw[t] = w;
+    }
+}
+
+// In-place radix-2 transform of C interleaved sequences of length L stored
+// as buf[j * C + c] in bit-reversed order; twiddle exp(2 pi i q/len) is
+// tw[q * (N / len)] (tw covers the full length N).
+template <typename C>
+__device__ void fft_smem(C* buf, int L, int logL, int Cn, const C* __restrict__ tw, int64_t N) {
+    const int nbf = (L >> 1) * Cn;
+    for (int s = 1; s <= logL; ++s) {
+        const int len = 1 << s, half = len >> 1;
+        const int64_t stride = N >> s;
+        for (int t = threadIdx.x; t < nbf; t += blockDim.x) {
+            const int c = t % Cn;
+            const int b = t / Cn;
+            const int q = b & (half - 1);
+            const int i0 = ((b >> (s - 1)) << s) + q;
+            const int i1 = i0 + half;
+            const C w = tw[q * stride];
+            const C u = buf[i0 * Cn + c];
+            const C v = cmul(buf[i1 * Cn + c], w);
+            buf[i0 * Cn + c] = cadd(u, v);
+            buf[i1 * Cn + c] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T> struct RecReader;
+template <> struct RecReader<double> {
+    const double* rec;
+    __device__ double operator()(int64_t row, int64_t N, int64_t j) const {
+        return rec[row * N + j];
+    }
+};
+template <> struct RecReader<float> {
+    const void* rec;
+    int kahan;   // 1: (sum, compensation) float pairs, 0: double
+    __device__ float operator()(int64_t row, int64_t N, int64_t j) const {
+        if (kahan) {
+            const float2 v = static_cast<const float2*>(rec)[row * N + j];
+            return v.x + v.y;
+        }
+        return (float)static_cast<const double*>(rec)[row * N + j];
+    }
+};
+
+struct SeqRows {   // the two real rows of complex sequence (pair, kind)
+    int64_t ra, rb;   // record rows (m * 3 + c), -1 = zero row
+    int64_t ma, mb;   // pixels receiving |A|^2 and |B|^2 (-1 = none)
+    int ca, cb;       // components of A and B
+};
+
+__device__ __forceinline__ SeqRows seq_rows(int64_t pair, int kind, int64_t n_pix) {
+    const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
+    const bool has1 = m1 < n_pix;
+    SeqRows s;
+    if (kind == 0) {
+        s.ra = m0 * 3 + 0; s.rb = m0 * 3 + 1; s.ma = m0; s.mb = m0; s.ca = 0; s.cb = 1;
+    } else if (kind == 1) {
+        s.ra = has1 ? m1 * 3 + 0 : -1; s.rb = has1 ? m1 * 3 + 1 : -1;
+        s.ma = has1 ? m1 : -1; s.mb = has1 ? m1 : -1; s.ca = 0; s.cb = 1;
+    } else {
+        s.ra = m0 * 3 + 2; s.rb = has1 ? m1 * 3 + 2 : -1;
+        s.ma = m0; s.mb = has1 ? m1 : -1; s.ca = 2; s.cb = 2;
+    }
+    return s;
+}
+
+// Split Z_l / Z_{N-l} into the two real rows' spectra and accumulate the powers.
+template <typename T, typename C>
+__device__ __forceinline__ void emit(const SeqRows& sr, int64_t l, C zl, C zn, int64_t nl,
+                                     T* __restrict__ S, C* __restrict__ X, bool atomic) {
+    C A, B;
+    A.x = (T)0.5 * (zl.x + zn.x);
+    A.y = (T)0.5 * (zl.y - zn.y);
+    B.x = (T)0.5 * (zl.y + zn.y);
+    B.y = (T)0.5 * (zn.x - zl.x);
+    const T pa = A.x * A.x + A.y * A.y;
+    const T pb = B.x * B.x + B.y * B.y;
+    if (sr.ma >= 0) {
+        if (atomic) atomicAdd(S + sr.ma * nl + l, pa);
+        else S[sr.ma * nl + l] += pa;
+        if (X) X[(sr.ma * 3 + sr.ca) * nl + l] = A;
+    }
+    if (sr.mb >= 0) {
+        if (atomic) atomicAdd(S + sr.mb * nl + l, pb);
+        else S[sr.mb * nl + l] += pb;
+        if (X) X[(sr.mb * 3 + sr.cb) * nl + l] = B;
+    }
+}
+
+// ---------------------------------------------------------------- direct path
+
+template <typename T>
+__global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, int logN, T scale,
+                                       const typename V2<T>::type* __restrict__ tw,
+                                       T* __restrict__ S, typename V2<T>::type* __restrict__ X) {
+    using C = typename V2<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int64_t pair = blockIdx.x;
+    const int64_t nl = N / 2 + 1;
+    for (int kind = 0; kind < 3; ++kind) {
+        const SeqRows sr = seq_rows(pair, kind, n_pix);
+        if (sr.ma < 0 && sr.mb < 0) continue;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            C z;
+            z.x = sr.ra >= 0 ? (scale * rd(sr.ra, N, j)) * scale : (T)0;
+            z.y = sr.rb >= 0 ? (scale * rd(sr.rb, N, j)) * scale : (T)0;
+            buf[bitrev(j, logN)] = z;
+        }
+        __syncthreads();
+        fft_smem<C>(buf, N, logN, 1, tw, N);
+        for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+            const int ln = (N - l) & (N - 1);
+            emit<T, C>(sr, l, buf[l], buf[ln], nl, S, X, false);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- four-step
+
+// Pass 1: tile of N1 rows x CT columns (columns j2 in [c0, c0+CT)) of sequence seq.
+template <typename T, int CT>
+__global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N1, int logN1,
+                                      int N2, T scale, const typename V2<T>::type* __restrict__ tw,
+                                      typename V2<T>::type* __restrict__ Y) {
+    using C = typename V2<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [N1][CT]
+    const int64_t seq = blockIdx.y;
+    const int c0 = blockIdx.x * CT;
+    const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
+    for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
+        const int c = t % CT, j1 = t / CT;
+        const int64_t j = (int64_t)j1 * N2 + c0 + c;
+        C z;
+        z.x = sr.ra >= 0 ? (scale * rd(sr.ra, N, j)) * scale : (T)0;
+        z.y = sr.rb >= 0 ? (scale * rd(sr.rb, N, j)) * scale : (T)0;
+        buf[bitrev(j1, logN1) * CT + c] = z;
+    }
+    __syncthreads();
+    fft_smem<C>(buf, N1, logN1, CT, tw, N);
+    C* Ys = Y + seq * (int64_t)N;
+    for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
+        const int c = t % CT, l1 = t / CT;
+        const int j2 = c0 + c;
+        const int64_t e = ((int64_t)j2 * l1) & (N - 1);
+        Ys[(int64_t)l1 * N2 + j2] = cmul(buf[l1 * CT + c], tw[e]);
+    }
+}
+
+// Pass 2: rows l1 and N1 - l1 of sequence seq; transforms and emits spectra.
+template <typename T>
+__global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2,
+                                      const typename V2<T>::type* __restrict__ tw,
+                                      const typename V2<T>::type* __restrict__ Y,
+                                      T* __restrict__ S, typename V2<T>::type* __restrict__ X) {
+    using C = typename V2<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][2]
+    const int64_t seq = blockIdx.y;
+    const int l1 = blockIdx.x;                  // 0 .. N1/2
+    const int l1p = (N1 - l1) & (N1 - 1);       // mirror row
+    const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
+    if (sr.ma < 0 && sr.mb < 0) return;
+    const C* Ys = Y + seq * (int64_t)N;
+    for (int t = threadIdx.x; t < 2 * N2; t += blockDim.x) {
+        const int c = t & 1, j2 = t >> 1;
+        const int row = c ? l1p : l1;
+        buf[bitrev(j2, logN2) * 2 + c] = Ys[(int64_t)row * N2 + j2];
+    }
+    __syncthreads();
+    fft_smem<C>(buf, N2, logN2, 2, tw, N);
+    const int64_t nl = N / 2 + 1;
+    const int64_t half = N / 2;
+    for (int t = threadIdx.x; t < 2 * N2; t += blockDim.x) {
+        const int c = t & 1, l2 = t >> 1;
+        if (c == 1 && l1p == l1) continue;            // self-mirrored row: once
+        const int row = c ? l1p : l1;
+        const int64_t l = row + (int64_t)N1 * l2;
+        if (l > half) continue;
+        // mirror index N - l lives in the other column
+        int l2m;
+        if (row == 0) l2m = (N2 - l2) & (N2 - 1);
+        else l2m = N2 - 1 - l2;
+        const C zl = buf[l2 * 2 + c];
+        const C zn = buf[l2m * 2 + (1 - c)];
+        emit<T, C>(sr, l, zl, zn, nl, S, X, true);
+    }
+}
+
+template <typename T> void set_reader(RecReader<T>& rd, const void* rec, int kahan);
+template <> void set_reader<double>(RecReader<double>& rd, const void* rec, int) {
+    rd.rec = static_cast<const double*>(rec);
+}
+template <> void set_reader<float>(RecReader<float>& rd, const void* rec, int kahan) {
+    rd.rec = rec;
+    rd.kahan = kahan;
+}
+
+template <typename T>
+int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g, double q,
+                 void* spectrum, void* X_save, void* ws, size_t* ws_bytes, cudaStream_t st) {
+    using C = typename V2<T>::type;
+    const int64_t N = g->n_bins;
+    int logN = 0;
+    while ((int64_t(1) << logN) < N) ++logN;
+    const bool direct = N <= 4096;
+    const int64_t n_pairs = (n_pix + 1) / 2;
+    const int64_t n_seq = 3 * n_pairs;
+    const size_t tw_bytes = align256(sizeof(C) * (size_t)N);
+    const size_t y_bytes = direct ? 0 : align256(sizeof(C) * (size_t)N * (size_t)n_seq);
+    const size_t need = tw_bytes + y_bytes;
+    if (!ws) {
+        *ws_bytes = need;
+        return LW_OK;
+    }
+    if (*ws_bytes < need) {
+        *ws_bytes = need;
+        return LW_ESIZE;
+    }
+    C* tw = reinterpret_cast<C*>(ws);
+    C* Y = reinterpret_cast<C*>(static_cast<char*>(ws) + tw_bytes);
+    const double K = q * q / (16.0 * kPi * kPi * kPi * kEps0 * kC0);
+    // inputs are multiplied twice by sqrt(sqrt(K) dt_u) so that no factor leaves the
+    // normal FP32 range: X' = sqrt(K) dt_u X and S = |X'|^2
+    const T scale = (T)sqrt(sqrt(K) * g->dt_u);
+    RecReader<T> rd;
+    set_reader<T>(rd, record, kahan);
+    T* S = static_cast<T*>(spectrum);
+    C* X = static_cast<C*>(X_save);
+    const int nl = (int)(N / 2 + 1);
+
+    const int tw_grid = (int)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
+    twiddle_kernel<T><<<tw_grid, 256, 0, st>>>(tw, N);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    if (cudaMemsetAsync(S, 0, sizeof(T) * (size_t)nl * (size_t)n_pix, st) != cudaSuccess)
+        return LW_ECUDA;
+    if (direct) {
+        const size_t smem = sizeof(C) * (size_t)N;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(spectrum_direct_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return LW_ECUDA;
+        spectrum_direct_kernel<T><<<(unsigned)n_pairs, 256, smem, st>>>(
+            rd, n_pix, (int)N, logN, scale, tw, S, X);
+        return launch_status();
+    }
+    const int logN2 = (logN + 1) / 2, logN1 = logN - logN2;
+    const int N1 = 1 << logN1, N2 = 1 << logN2;
+    constexpr int CT = 16;
+    {
+        const size_t smem = sizeof(C) * (size_t)N1 * CT;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(spectrum_pass1_kernel<T, CT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return LW_ECUDA;
+        dim3 grid((unsigned)(N2 / CT), (unsigned)n_seq);
+        spectrum_pass1_kernel<T, CT><<<grid, 256, smem, st>>>(rd, n_pix, (int)N, N1, logN1, N2,
+                                                              scale, tw, Y);
+        if (launch_status() != LW_OK) return LW_ECUDA;
+    }
+    {
+        const size_t smem = sizeof(C) * (size_t)N2 * 2;
+        dim3 grid((unsigned)(N1 / 2 + 1), (unsigned)n_seq);
+        spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw, Y,
+                                                          S, X);
+        return launch_status();
+    }
+}
+
+}  // namespace
+}  // namespace lw
+
+using namespace lw;
+
+extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
+                           const lw_grid* grid, double q, void* spectrum, void* X_save, void* ws,
+                           size_t* ws_bytes, void* stream) {
+    if (!grid || !ws_bytes || n_pix < 1) return LW_EINVAL;
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+        return LW_EINVAL;
+    const int64_t N = grid->n_bins;
+    if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;
+    if (!(grid->dt_u > 0.0) || !isfinite(q)) return LW_EINVAL;
+    if (ws && (!record || !spectrum)) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (precision == LW_FP64)
+        return run_spectrum<double>(record, 0, n_pix, grid, q, spectrum, X_save, ws, ws_bytes,
+                                    st);
+    return run_spectrum<float>(record, precision == LW_MIXED_KAHAN, n_pix, grid, q, spectrum,
+                               X_save, ws, ws_bytes, st);
+}

@@ -1,0 +1,293 @@
+// Trajectory upload (device layout) and observer-grid bounds.
+//
+// lw_trajectories_upload builds up to two device sections from the caller's
+// FP64 trajectories:
+//   FP64   plain copies of t, r, beta, beta_dot (inputs of the FP64 deposit);
+//   MIXED  per sample a float4 (tau - tau_b, x - x_b, y - y_b, z - z_b) with the
+//          light-front time tau = t - z/c0 taken relative to the first sample of
+//          the sample's anchoring block, six floats of field data
+//          (beta_x, beta_y, 1 - beta_z, beta_dot), and per block the FP64 anchor
+//          (tau_b, x_b, y_b, z_b).  Subtracting the anchor in FP64 keeps the FP32
+//          numbers small, so the FP32 part of the bin coordinate stays accurate.
+// lw_grid_bounds evaluates Eqs. (tu_min) and (tu_max).
+#include <math.h>
+
+#include "lw_internal.cuh"
+
+namespace lw {
+namespace {
+
+struct TrajLayout {
+    size_t status = 0, ends = 0, t = 0, r = 0, beta = 0, beta_dot = 0, scan = 0, field = 0,
+           anchor = 0;
+    size_t total = 0;
+    int64_t n_t = 0;
+    int n_blocks = 0;
+};
+
+TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int block) {
+    TrajLayout L;
+    const int64_t ns1 = n_s + 1;
+    L.n_t = (t_per_e ? n_e : 1) * ns1;
+    L.n_blocks = (int)((ns1 + block - 1) / block);
+    size_t off = 0;
+    L.status = off;
+    off = align256(off + sizeof(int32_t));
+    L.ends = off;
+    off = align256(off + sizeof(double) * 8 * (size_t)n_e);
+    if (sections & LW_SECTION_FP64) {
+        L.t = off;
+        off = align256(off + sizeof(double) * (size_t)L.n_t);
+        L.r = off;
+        off = align256(off + sizeof(double) * 3 * (size_t)(n_e * ns1));
+        L.beta = off;
+        off = align256(off + sizeof(double) * 3 * (size_t)(n_e * ns1));
+        L.beta_dot = off;
+        off = align256(off + sizeof(double) * 3 * (size_t)(n_e * ns1));
+    }
+    if (sections & LW_SECTION_MIXED) {
+        L.scan = off;
+        off = align256(off + sizeof(float4) * (size_t)(n_e * ns1));
+        L.field = off;
+        off = align256(off + sizeof(float) * 6 * (size_t)(n_e * ns1));
+        L.anchor = off;
+        off = align256(off + sizeof(D4) * (size_t)(n_e * L.n_blocks));
+    }
+    L.total = off;
+    return L;
+}
+
+// Input checks of every sample: finite values, |beta| < 1 (evaluated as
+// ((bx*bx + by*by) + bz*bz) < 1), strictly increasing lab time.
+__global__ void check_inputs_kernel(const double* __restrict__ t, int t_per_e,
+                                    const double* __restrict__ r,
+                                    const double* __restrict__ beta,
+                                    const double* __restrict__ bdot, int64_t n_e, int64_t ns1,
+                                    int32_t* __restrict__ status) {
+    const int64_t total = n_e * ns1;
+    int bits = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = s / ns1;
+        const int64_t i = s - k * ns1;
+        const double* x = r + 3 * s;
+        const double* b = beta + 3 * s;
+        const double* a = bdot + 3 * s;
+        bool fin = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(b[0]) &&
+                   isfinite(b[1]) && isfinite(b[2]) && isfinite(a[0]) && isfinite(a[1]) &&
+                   isfinite(a[2]);
+        if (!fin) bits |= LW_ST_NONFINITE;
+        double b2 = __dadd_rn(__dadd_rn(__dmul_rn(b[0], b[0]), __dmul_rn(b[1], b[1])),
+                              __dmul_rn(b[2], b[2]));
+        if (!(b2 < 1.0)) bits |= LW_ST_BETA;
+        if (t_per_e || k == 0) {
+            const double* tk = t + (t_per_e ? k * ns1 : 0);
+            if (!isfinite(tk[i])) bits |= LW_ST_NONFINITE;
+            if (i > 0 && !(tk[i] > tk[i - 1])) bits |= LW_ST_TIME;
+        }
+    }
+    block_status_or(status, bits);
+}
+
+__global__ void build_mixed_kernel(const double* __restrict__ t, int t_per_e,
+                                   const double* __restrict__ r,
+                                   const double* __restrict__ beta,
+                                   const double* __restrict__ bdot, int64_t n_e, int64_t ns1,
+                                   int block, int n_blocks, float4* __restrict__ scan,
+                                   float* __restrict__ field, D4* __restrict__ anchor) {
+    const int64_t total = n_e * ns1;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = s / ns1;
+        const int64_t i = s - k * ns1;
+        const int64_t ib = (i / block) * block;
+        const int64_t sb = k * ns1 + ib;
+        const double* tk = t + (t_per_e ? k * ns1 : 0);
+        const double x = r[3 * s], y = r[3 * s + 1], z = r[3 * s + 2];
+        const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
+        const double tau = tk[i] - z * kInvC0;
+        const double taub = tk[ib] - zb * kInvC0;
+        scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
+                              (float)(z - zb));
+        const double* b = beta + 3 * s;
+        const double* a = bdot + 3 * s;
+        float* f = field + 6 * s;
+        f[0] = (float)b[0];
+        f[1] = (float)b[1];
+        f[2] = (float)(1.0 - b[2]);
+        f[3] = (float)a[0];
+        f[4] = (float)a[1];
+        f[5] = (float)a[2];
+        if (i == ib) anchor[k * n_blocks + i / block] = D4{taub, xb, yb, zb};
+    }
+}
+
+__global__ void ends_kernel(const double* __restrict__ t, int t_per_e,
+                            const double* __restrict__ r, int64_t n_e, int64_t ns1,
+                            double* __restrict__ ends) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double* tk = t + (t_per_e ? k * ns1 : 0);
+        const double* x0 = r + 3 * (k * ns1);
+        const double* x1 = r + 3 * (k * ns1 + ns1 - 1);
+        double* e = ends + 8 * k;
+        e[0] = tk[0];
+        e[1] = x0[0];
+        e[2] = x0[1];
+        e[3] = x0[2];
+        e[4] = tk[ns1 - 1];
+        e[5] = x1[0];
+        e[6] = x1[1];
+        e[7] = x1[2];
+    }
+}
+
+__global__ void bounds_init_kernel(unsigned long long* keys) {
+    keys[0] = ordered_key(INFINITY);
+    keys[1] = ordered_key(-INFINITY);
+}
+
+// One thread per (pixel, electron); Eqs. (tu_min), (tu_max).
+__global__ void bounds_kernel(const double* __restrict__ ends, int64_t n_e,
+                              const double* __restrict__ n_hat, int64_t n_pix,
+                              unsigned long long* keys) {
+    double lo = INFINITY, hi = -INFINITY;
+    const int64_t total = n_e * n_pix;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = s / n_e;
+        const int64_t k = s - m * n_e;
+        const double nx = n_hat[3 * m], ny = n_hat[3 * m + 1], nz = n_hat[3 * m + 2];
+        const double* e = ends + 8 * k;
+        double a0 = advanced_time_fp64(nx, ny, nz, e[1], e[2], e[3], e[0]);
+        double a1 = advanced_time_fp64(nx, ny, nz, e[5], e[6], e[7], e[4]);
+        lo = fmin(lo, a0);
+        hi = fmax(hi, a1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&keys[0], ordered_key(lo));
+        atomicMax(&keys[1], ordered_key(hi));
+    }
+}
+
+__global__ void bounds_finish_kernel(unsigned long long* keys) {
+    double* out = reinterpret_cast<double*>(keys);
+    double lo = key_to_double(keys[0]);
+    double hi = key_to_double(keys[1]);
+    out[0] = lo;
+    out[1] = hi;
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)kSms * 32;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+}  // namespace lw
+
+using namespace lw;
+
+extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, int32_t block,
+                                      void* ws, size_t* ws_bytes, lw_traj* out, void* stream) {
+    if (!in || !ws_bytes || !out) return LW_EINVAL;
+    if (in->n_e < 1 || in->n_s < 1) return LW_EINVAL;
+    if (!in->t || !in->r || !in->beta || !in->beta_dot) return LW_EINVAL;
+    if (sections <= 0 || (sections & ~(LW_SECTION_FP64 | LW_SECTION_MIXED))) return LW_EINVAL;
+    if (block == 0) block = 128;
+    if (block < 16 || block > 1024 || (block & (block - 1))) return LW_EINVAL;
+    const int t_per_e = in->t_per_electron ? 1 : 0;
+    const TrajLayout L = make_layout(in->n_e, in->n_s, t_per_e, sections, block);
+    if (!ws) {
+        *ws_bytes = L.total;
+        return LW_OK;
+    }
+    if (*ws_bytes < L.total) {
+        *ws_bytes = L.total;
+        return LW_ESIZE;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    char* base = static_cast<char*>(ws);
+    const int64_t ns1 = in->n_s + 1;
+    const size_t vec_bytes = sizeof(double) * 3 * (size_t)(in->n_e * ns1);
+
+    lw_traj v{};
+    v.n_e = in->n_e;
+    v.n_s = in->n_s;
+    v.t_per_electron = t_per_e;
+    v.sections = sections;
+    v.block = block;
+    v.n_blocks = L.n_blocks;
+    int32_t* status = reinterpret_cast<int32_t*>(base + L.status);
+    v.input_status = status;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return LW_ECUDA;
+
+    const double *t = in->t, *r = in->r, *beta = in->beta, *bdot = in->beta_dot;
+    if (sections & LW_SECTION_FP64) {
+        double* dt = reinterpret_cast<double*>(base + L.t);
+        double* dr = reinterpret_cast<double*>(base + L.r);
+        double* db = reinterpret_cast<double*>(base + L.beta);
+        double* dd = reinterpret_cast<double*>(base + L.beta_dot);
+        if (cudaMemcpyAsync(dt, in->t, sizeof(double) * (size_t)L.n_t, cudaMemcpyDefault, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(dr, in->r, vec_bytes, cudaMemcpyDefault, st) != cudaSuccess ||
+            cudaMemcpyAsync(db, in->beta, vec_bytes, cudaMemcpyDefault, st) != cudaSuccess ||
+            cudaMemcpyAsync(dd, in->beta_dot, vec_bytes, cudaMemcpyDefault, st) != cudaSuccess)
+            return LW_ECUDA;
+        v.t = dt;
+        v.r = dr;
+        v.beta = db;
+        v.beta_dot = dd;
+        t = dt;
+        r = dr;
+        beta = db;
+        bdot = dd;
+    }
+    const int threads = 256;
+    double* ends = reinterpret_cast<double*>(base + L.ends);
+    ends_kernel<<<grid_for(in->n_e, threads), threads, 0, st>>>(t, t_per_e, r, in->n_e, ns1,
+                                                                 ends);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    v.ends = ends;
+    check_inputs_kernel<<<grid_for(in->n_e * ns1, threads), threads, 0, st>>>(
+        t, t_per_e, r, beta, bdot, in->n_e, ns1, status);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    if (sections & LW_SECTION_MIXED) {
+        float4* scan = reinterpret_cast<float4*>(base + L.scan);
+        float* field = reinterpret_cast<float*>(base + L.field);
+        D4* anchor = reinterpret_cast<D4*>(base + L.anchor);
+        build_mixed_kernel<<<grid_for(in->n_e * ns1, threads), threads, 0, st>>>(
+            t, t_per_e, r, beta, bdot, in->n_e, ns1, block, L.n_blocks, scan, field, anchor);
+        if (launch_status() != LW_OK) return LW_ECUDA;
+        v.scan = scan;
+        v.field = field;
+        v.anchor = reinterpret_cast<const double*>(anchor);
+    }
+    *out = v;
+    *ws_bytes = L.total;
+    return LW_OK;
+}
+
+extern "C" int lw_grid_bounds(const lw_traj* traj, const lw_detector* det, double* bounds,
+                              void* stream) {
+    if (!traj || !det || !bounds || !det->n_hat || det->n_pix < 1) return LW_EINVAL;
+    if (!traj->ends || traj->n_e < 1) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(bounds);
+    bounds_init_kernel<<<1, 1, 0, st>>>(keys);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    const int threads = 256;
+    bounds_kernel<<<grid_for(traj->n_e * det->n_pix, threads), threads, 0, st>>>(
+        traj->ends, traj->n_e, det->n_hat, det->n_pix, keys);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    bounds_finish_kernel<<<1, 1, 0, st>>>(keys);
+    return launch_status();
+}

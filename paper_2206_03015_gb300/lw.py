@@ -1,0 +1,297 @@
+"""Python binding of liblw.so (argument marshalling only).
+
+Every function here forwards to the C ABI of ``include/lw.h`` with the same
+name; PyTorch supplies device memory and the current CUDA stream.  All
+arithmetic of the radiation method runs in the library's CUDA kernels.  There
+is no CPU fallback: if the library or a GPU is missing, loading fails with an
+error.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+LW_OK, LW_EINVAL, LW_ESIZE, LW_ECUDA, LW_EUNSUPPORTED, LW_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LW_FP64, LW_MIXED, LW_MIXED_KAHAN = 0, 1, 2
+LW_FIELD_ACCEL, LW_FIELD_VELOCITY = 1, 2
+LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER = 1, 2, 4, 8, 16
+LW_SECTION_FP64, LW_SECTION_MIXED = 1, 2
+
+Q_E = 1.602176634e-19
+
+_ERRORS = {LW_EINVAL: "invalid argument", LW_ESIZE: "workspace too small",
+           LW_ECUDA: "CUDA launch failed", LW_EUNSUPPORTED: "unsupported size",
+           LW_ETIMEOUT: "device wait timed out"}
+
+
+class LWError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {code} ({_ERRORS.get(code, 'unknown')})")
+        self.code = code
+
+
+class lw_traj_in(ctypes.Structure):
+    _fields_ = [("n_e", ctypes.c_int64), ("n_s", ctypes.c_int64), ("t", ctypes.c_void_p),
+                ("t_per_electron", ctypes.c_int32), ("r", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("beta_dot", ctypes.c_void_p)]
+
+
+class lw_traj(ctypes.Structure):
+    _fields_ = [("n_e", ctypes.c_int64), ("n_s", ctypes.c_int64),
+                ("t_per_electron", ctypes.c_int32), ("sections", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("t", ctypes.c_void_p), ("r", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("beta_dot", ctypes.c_void_p), ("scan", ctypes.c_void_p),
+                ("field", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
+                ("ends", ctypes.c_void_p), ("input_status", ctypes.c_void_p)]
+
+
+class lw_detector(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int64), ("n_hat", ctypes.c_void_p), ("R", ctypes.c_double)]
+
+
+class lw_grid(ctypes.Structure):
+    _fields_ = [("t_min", ctypes.c_double), ("dt_u", ctypes.c_double),
+                ("n_bins", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain", "lw_spectrum")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblw.so (building it first if needed); raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"liblw.so not built ({path})")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        lib.lw_trajectories_upload.argtypes = [ctypes.POINTER(lw_traj_in), ctypes.c_int32,
+                                               ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t),
+                                               ctypes.POINTER(lw_traj), P]
+        lib.lw_grid_bounds.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector), P, P]
+        lib.lw_deposit_time_domain.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector),
+                                               ctypes.POINTER(lw_grid), ctypes.c_int32,
+                                               ctypes.c_uint32, P, ctypes.c_int32, P, P]
+        lib.lw_spectrum.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(lw_grid),
+                                    ctypes.c_double, P, P, P, ctypes.POINTER(ctypes.c_size_t), P]
+        for f in EXPORTS:
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2206_03015_gb300 needs a CUDA GPU; no CPU fallback exists")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(fn, rc):
+    if rc != LW_OK:
+        raise LWError(fn, rc)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A 256-byte aligned device byte buffer (for the library's workspaces)."""
+    return _aligned_bytes(nbytes, device)
+
+
+def _aligned_bytes(nbytes: int, device) -> torch.Tensor:
+    buf = torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + max(int(nbytes), 1)]
+
+
+@dataclass
+class Grid:
+    """Uniform observer grid t_j = t_min + j dt_u (j = 0..n_bins-1)."""
+    t_min: float
+    dt_u: float
+    n_bins: int
+
+    def c(self) -> lw_grid:
+        return lw_grid(float(self.t_min), float(self.dt_u), int(self.n_bins))
+
+    @property
+    def omega(self):
+        """Angular frequencies omega_l = 2 pi l/(n_bins dt_u), l = 0..n_bins/2."""
+        return torch.arange(self.n_bins // 2 + 1, dtype=torch.float64) * (
+            2.0 * math.pi / (self.n_bins * self.dt_u))
+
+
+def grid_from_bounds(t_min: float, t_max: float, n_bins: int) -> Grid:
+    """dt_u = (t_max - t_min) / n_bins, so that d_omega = 2 pi / T_u exactly."""
+    return Grid(float(t_min), (float(t_max) - float(t_min)) / int(n_bins), int(n_bins))
+
+
+class Detector:
+    """Pixel directions n_hat [n_pix][3] (float64, on the GPU) at radius R."""
+
+    def __init__(self, n_hat, R: float = 1.0, device="cuda"):
+        self.n_hat = torch.as_tensor(n_hat, dtype=torch.float64).to(device).contiguous()
+        assert self.n_hat.ndim == 2 and self.n_hat.shape[1] == 3
+        self.R = float(R)
+
+    @property
+    def n_pix(self):
+        return self.n_hat.shape[0]
+
+    def c(self) -> lw_detector:
+        return lw_detector(self.n_pix, self.n_hat.data_ptr(), self.R)
+
+
+class Trajectories:
+    """Uploaded trajectories: the workspace tensor plus the C view into it."""
+
+    def __init__(self, ws, view: lw_traj):
+        self.ws = ws
+        self.view = view
+
+    @property
+    def n_e(self):
+        return self.view.n_e
+
+    @property
+    def n_s(self):
+        return self.view.n_s
+
+
+def _as_input(x, device):
+    if not isinstance(x, torch.Tensor):
+        x = torch.from_numpy(x)
+    x = x.to(torch.float64)
+    if x.device.type == "cpu" and not x.is_pinned():
+        x = x.to(device)
+    return x.contiguous()
+
+
+def lw_trajectories_upload(t, r, beta, beta_dot, sections=LW_SECTION_FP64 | LW_SECTION_MIXED,
+                           block: int = 128, device="cuda", ws=None) -> Trajectories:
+    """Copy trajectories (t, r, beta, beta_dot; CUDA or pinned-CPU float64 tensors,
+    or numpy arrays) into the device layout (see lw.h).  ``ws`` may pass a
+    previously returned workspace (``Trajectories.ws``) for reuse."""
+    _require_cuda()
+    lib = load()
+    t, r, beta, beta_dot = (_as_input(a, device) for a in (t, r, beta, beta_dot))
+    n_e, ns1, three = r.shape
+    assert three == 3 and beta.shape == r.shape and beta_dot.shape == r.shape
+    t_per_e = 1 if t.ndim == 2 else 0
+    inp = lw_traj_in(n_e, ns1 - 1, t.data_ptr(), t_per_e, r.data_ptr(), beta.data_ptr(),
+                     beta_dot.data_ptr())
+    nbytes = ctypes.c_size_t(0)
+    view = lw_traj()
+    _check("lw_trajectories_upload",
+           lib.lw_trajectories_upload(ctypes.byref(inp), sections, block, None,
+                                      ctypes.byref(nbytes), ctypes.byref(view), None))
+    if ws is None or ws.numel() < nbytes.value or ws.data_ptr() % 256:
+        ws = _aligned_bytes(nbytes.value, device)
+    nbytes = ctypes.c_size_t(ws.numel())
+    _check("lw_trajectories_upload",
+           lib.lw_trajectories_upload(ctypes.byref(inp), sections, block, _ptr(ws),
+                                      ctypes.byref(nbytes), ctypes.byref(view), _stream()))
+    traj = Trajectories(ws, view)
+    traj._inputs = (t, r, beta, beta_dot)   # keep host/pinned sources alive until the copy ran
+    return traj
+
+
+def lw_grid_bounds(traj: Trajectories, det: Detector, out=None):
+    """Device double[2] = (t_u^min, t_u^max) of Eqs. (tu_min), (tu_max)."""
+    lib = load()
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=det.n_hat.device)
+    d = det.c()
+    _check("lw_grid_bounds", lib.lw_grid_bounds(ctypes.byref(traj.view), ctypes.byref(d),
+                                                _ptr(out), _stream()))
+    return out
+
+
+def record_shape(det: Detector, grid: Grid, precision: int):
+    """(shape, dtype) of the record: FP64 and MIXED accumulate in float64,
+    MIXED_KAHAN in (sum, compensation) float32 pairs."""
+    if precision in (LW_FP64, LW_MIXED):
+        return (det.n_pix, 3, grid.n_bins), torch.float64
+    return (det.n_pix, 3, grid.n_bins, 2), torch.float32
+
+
+def record_value(record: torch.Tensor, precision: int) -> torch.Tensor:
+    """The record as float64 [n_pix][3][n_bins] (sum + compensation for MIXED_KAHAN)."""
+    if precision == LW_MIXED_KAHAN:
+        return record[..., 0].double() + record[..., 1].double()
+    return record
+
+
+def lw_deposit_time_domain(traj: Trajectories, det: Detector, grid: Grid, precision: int,
+                           field_flags: int = LW_FIELD_ACCEL, record=None, accumulate=False,
+                           status=None):
+    """Algorithm 2 for every pixel; returns the record (see record_shape)."""
+    lib = load()
+    shape, dtype = record_shape(det, grid, precision)
+    if record is None:
+        record = torch.empty(shape, dtype=dtype, device=det.n_hat.device)
+        accumulate = False
+    assert tuple(record.shape) == shape and record.dtype == dtype and record.is_contiguous()
+    d = det.c()
+    g = grid.c()
+    _check("lw_deposit_time_domain",
+           lib.lw_deposit_time_domain(ctypes.byref(traj.view), ctypes.byref(d), ctypes.byref(g),
+                                      precision, field_flags, _ptr(record), int(bool(accumulate)),
+                                      _ptr(status), _stream()))
+    return record
+
+
+def spectrum_workspace_bytes(precision: int, n_pix: int, grid: Grid) -> int:
+    lib = load()
+    nbytes = ctypes.c_size_t(0)
+    g = grid.c()
+    _check("lw_spectrum", lib.lw_spectrum(None, precision, n_pix, ctypes.byref(g), Q_E, None,
+                                          None, None, ctypes.byref(nbytes), None))
+    return nbytes.value
+
+
+def lw_spectrum(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E, want_X=False,
+                ws=None, out=None):
+    """S [n_pix][n_bins/2+1] (FP64 or FP32) and optionally X' [n_pix][3][n_bins/2+1] complex."""
+    lib = load()
+    dev = record.device
+    dtype = torch.float64 if precision == LW_FP64 else torch.float32
+    nl = grid.n_bins // 2 + 1
+    S = out if out is not None else torch.empty((n_pix, nl), dtype=dtype, device=dev)
+    X = torch.empty((n_pix, 3, nl, 2), dtype=dtype, device=dev) if want_X else None
+    need = spectrum_workspace_bytes(precision, n_pix, grid)
+    if ws is None or ws.numel() < need:
+        ws = _aligned_bytes(need, dev)
+    nbytes = ctypes.c_size_t(ws.numel())
+    g = grid.c()
+    _check("lw_spectrum", lib.lw_spectrum(_ptr(record), precision, n_pix, ctypes.byref(g), q,
+                                          _ptr(S), _ptr(X), _ptr(ws), ctypes.byref(nbytes),
+                                          _stream()))
+    if want_X:
+        return S, torch.view_as_complex(X)
+    return S

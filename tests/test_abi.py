@@ -1,0 +1,97 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/lw.h declares; host-side argument checks and size queries work
+without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2206_03015_gb300 import build as lwbuild
+from paper_2206_03015_gb300 import lw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            with open(os.path.join(ROOT, "include", h)) as f:
+                text = f.read()
+            names += re.findall(r"^int\s+(lw_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lwbuild.build()
+    return lw.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain",
+              "lw_spectrum"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(lw.library_path())
+    for n in declared_functions():
+        assert hasattr(raw, n), n
+
+
+def test_upload_argument_checks_and_size_query(lib):
+    nbytes = ctypes.c_size_t(0)
+    view = lw.lw_traj()
+    assert lib.lw_trajectories_upload(None, 3, 64, None, ctypes.byref(nbytes),
+                                      ctypes.byref(view), None) == lw.LW_EINVAL
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced by a size query
+    inp = lw.lw_traj_in(10, 99, fake, 0, fake, fake, fake)
+    assert lib.lw_trajectories_upload(ctypes.byref(inp), 3, 64, None, ctypes.byref(nbytes),
+                                      ctypes.byref(view), None) == lw.LW_OK
+    # status + ends + FP64 copies + mixed section, each 256-byte aligned
+    ns1, ne = 100, 10
+    al = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    fp64 = al(8 * ns1) + 3 * al(8 * 3 * ne * ns1)
+    mixed = al(16 * ne * ns1) + al(24 * ne * ns1) + al(32 * ne * 2)
+    assert nbytes.value == al(4) + al(64 * ne) + fp64 + mixed
+    for bad_block in (8, 100, 2048):
+        assert lib.lw_trajectories_upload(ctypes.byref(inp), 3, bad_block, None,
+                                          ctypes.byref(nbytes), ctypes.byref(view),
+                                          None) == lw.LW_EINVAL
+    bad = lw.lw_traj_in(0, 99, fake, 0, fake, fake, fake)
+    assert lib.lw_trajectories_upload(ctypes.byref(bad), 3, 64, None, ctypes.byref(nbytes),
+                                      ctypes.byref(view), None) == lw.LW_EINVAL
+
+
+def test_deposit_argument_checks(lib):
+    view = lw.lw_traj()
+    view.sections = lw.LW_SECTION_FP64
+    det = lw.lw_detector(4, 0x1000, 1.0)
+    rec = ctypes.c_void_p(0x2000)
+    for g, flags, prec in ((lw.lw_grid(0.0, 0.0, 16), 1, 0),         # dt_u = 0
+                           (lw.lw_grid(0.0, 1e-18, 0), 1, 0),        # no bins
+                           (lw.lw_grid(0.0, 1e-18, 16), 0, 0),       # no field term
+                           (lw.lw_grid(0.0, 1e-18, 16), 1, 1),       # mixed section missing
+                           (lw.lw_grid(0.0, 1e-18, 16), 1, 7)):      # unknown precision
+        assert lib.lw_deposit_time_domain(ctypes.byref(view), ctypes.byref(det),
+                                          ctypes.byref(g), prec, flags, rec, 0, None,
+                                          None) == lw.LW_EINVAL
+
+
+def test_spectrum_size_query_and_limits(lib):
+    nbytes = ctypes.c_size_t(0)
+    g = lw.lw_grid(0.0, 1e-18, 4096)
+    assert lib.lw_spectrum(None, lw.LW_FP64, 10, ctypes.byref(g), 1.6e-19, None, None, None,
+                           ctypes.byref(nbytes), None) == lw.LW_OK
+    assert nbytes.value == 4096 * 16                      # twiddle table only
+    g = lw.lw_grid(0.0, 1e-18, 65536)
+    assert lib.lw_spectrum(None, lw.LW_MIXED, 10, ctypes.byref(g), 1.6e-19, None, None, None,
+                           ctypes.byref(nbytes), None) == lw.LW_OK
+    assert nbytes.value == 65536 * 8 + 3 * 5 * 65536 * 8  # twiddles + four-step buffer
+    for n in (3, 1000, 1 << 19):
+        g = lw.lw_grid(0.0, 1e-18, n)
+        assert lib.lw_spectrum(None, lw.LW_FP64, 10, ctypes.byref(g), 1.6e-19, None, None, None,
+                               ctypes.byref(nbytes), None) == lw.LW_EUNSUPPORTED

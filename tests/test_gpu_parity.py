@@ -1,0 +1,151 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element,
+on seeded inputs that span several tiles and ragged tails, plus edge cases.
+
+Tolerances: FP64 path 1e-9 relative L2 (records and spectra); the advanced
+times and bin indices are bit-identical by construction, so the observed
+error is summation order only (~1e-15).  Mixed path 1e-4 relative L2 on
+spectra (FP32 field and FFT, FP64-exact bin coordinates)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_cases import gpu_bounds, gpu_run, oracle_run, rel_l2
+from paper_2206_03015_gb300 import lw
+from workloads import configs, simple
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+MIXED_TOL = 1e-4
+
+
+def _dirs(n, seed, max_angle):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tx = rng.uniform(-max_angle, max_angle, n)
+    ty = rng.uniform(-max_angle, max_angle, n)
+    return np.stack([np.sin(tx), np.cos(tx) * np.sin(ty), np.cos(tx) * np.cos(ty)], -1)
+
+
+def _case(name):
+    """(trajectories, n_hat, grid, flags, R) for the named parity case."""
+    if name == "ragged":           # 3 electrons x 38 samples, 129 pixels, 300 bins, clipping
+        tr = simple.random_smooth(3, 37, 3e-18, 101, gamma=6.0, amp=0.5)
+        n_hat = _dirs(129, 1, 0.2)
+        lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+        grid = lw.Grid(lo + 0.1 * (hi - lo), (hi - lo) / 280.0, 300)
+        return tr, n_hat, grid, lw.LW_FIELD_ACCEL, 1.0
+    if name == "t_per_electron":
+        tr = simple.random_smooth(5, 150, 2e-18, 102, gamma=4.0, amp=0.4, t_per_electron=True)
+        n_hat = _dirs(77, 2, 0.3)
+        lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+        grid = lw.Grid(lo, (hi - lo) / 512, 512)
+        return tr, n_hat, grid, lw.LW_FIELD_ACCEL, 1.0
+    if name == "velocity_field":
+        tr = simple.random_smooth(4, 200, 2e-18, 103, gamma=3.0, amp=0.5)
+        n_hat = _dirs(64, 3, 0.5)
+        lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+        grid = lw.Grid(lo, (hi - lo) / 1024, 1024)
+        return tr, n_hat, grid, lw.LW_FIELD_ACCEL | lw.LW_FIELD_VELOCITY, 1e-4
+    if name == "many_bins_per_step":   # b >> 1: each step covers many grid points
+        tr = simple.random_smooth(2, 40, 5e-18, 104, gamma=2.0, amp=0.5)
+        n_hat = _dirs(33, 4, 0.4)
+        lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+        grid = lw.Grid(lo, (hi - lo) / 4096, 4096)
+        return tr, n_hat, grid, lw.LW_FIELD_ACCEL, 1.0
+    if name == "c1_small":             # C1 physics at reduced size
+        w = configs.c1_tiny(n_e=16, n_s=2000, nx=8, n_bins=4096)
+        lo, hi = oracle.grid_bounds(w.traj.t, w.traj.r, w.n_hat)
+        return w.traj, w.n_hat, lw.grid_from_bounds(lo, hi, 4096), lw.LW_FIELD_ACCEL, 1.0
+    if name == "c1_offsets":
+        w = configs.c1_offsets(n_e=16, n_s=2000, nx=8, n_bins=4096)
+        lo, hi = oracle.grid_bounds(w.traj.t, w.traj.r, w.n_hat)
+        return w.traj, w.n_hat, lw.grid_from_bounds(lo, hi, 4096), lw.LW_FIELD_ACCEL, 1.0
+    if name == "single":               # degenerate: one electron, one step, one pixel, one bin
+        tr = simple.stationary_constant_acceleration(1, 1e-18, (1e15, 2e15, 0.0), t0=0.0)
+        n_hat = np.array([[0.0, 0.0, 1.0]])
+        return tr, n_hat, lw.Grid(0.5e-18, 1e-18, 1), lw.LW_FIELD_ACCEL, 1.0
+    if name == "all_clipped":          # grid after the whole arrival window
+        tr = simple.random_smooth(2, 30, 3e-18, 105, gamma=5.0)
+        n_hat = _dirs(5, 5, 0.2)
+        lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+        return tr, n_hat, lw.Grid(hi + (hi - lo), (hi - lo) / 64, 64), lw.LW_FIELD_ACCEL, 1.0
+    raise KeyError(name)
+
+
+CASES = ["ragged", "t_per_electron", "velocity_field", "many_bins_per_step", "c1_small",
+         "c1_offsets", "single", "all_clipped"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_grid_bounds_bit_exact(name):
+    tr, n_hat, _, _, _ = _case(name)
+    assert gpu_bounds(tr, n_hat) == oracle.grid_bounds(tr.t, tr.r, n_hat)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp64_record_and_spectrum(name):
+    tr, n_hat, grid, flags, R = _case(name)
+    g = gpu_run(tr, n_hat, grid, lw.LW_FP64, flags, R)
+    o = oracle_run(tr, n_hat, grid, flags, R)
+    assert g["status"] == o["status"]
+    scale = max(np.abs(o["rec"]).max(), 1e-300)
+    assert np.max(np.abs(g["rec"] - o["rec"])) <= 1e-12 * scale
+    assert rel_l2(g["rec"], o["rec"]) <= FP64_TOL
+    if "S" in o:
+        assert rel_l2(g["S"], o["S"]) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("block", [16, 128, 1024])
+@pytest.mark.parametrize("precision", [lw.LW_MIXED, lw.LW_MIXED_KAHAN])
+def test_mixed_record_and_spectrum(name, block, precision):
+    tr, n_hat, grid, flags, R = _case(name)
+    g = gpu_run(tr, n_hat, grid, precision, flags, R, block=block)
+    o = oracle_run(tr, n_hat, grid, flags, R)
+    # the mixed path reports input faults like the oracle; CLIP can differ when the last
+    # arrival lies within FP32 rounding of a grid point, and it does not report TA_ORDER
+    ignore = oracle.ST_TA_ORDER | oracle.ST_CLIP
+    assert (g["status"] & ~ignore) == (o["status"] & ~ignore)
+    if np.abs(o["rec"]).max() == 0:
+        assert np.abs(g["rec"]).max() == 0
+        return
+    assert rel_l2(g["rec"], o["rec"]) <= MIXED_TOL
+    if "S" in o:
+        assert rel_l2(g["S"], o["S"]) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("n_bins", [2, 4, 64, 1024, 4096, 8192, 65536, 131072])
+@pytest.mark.parametrize("n_pix", [1, 2, 5])
+def test_spectrum_matches_oracle(n_bins, n_pix):
+    rng = np.random.Generator(np.random.PCG64(n_bins + n_pix))
+    rec = rng.normal(size=(n_pix, 3, n_bins)) * 1e20
+    dt_u = 3.7e-18
+    grid = lw.Grid(0.0, dt_u, n_bins)
+    S_o, X_o = oracle.spectrum(rec, dt_u, want_X=True)
+    K = 1.602176634e-19**2 / (16 * math.pi**3 * 8.8541878128e-12 * 299792458.0)
+    X_o = X_o * math.sqrt(K) * dt_u
+    S_g, X_g = lw.lw_spectrum(torch.from_numpy(rec).cuda(), lw.LW_FP64, n_pix, grid, want_X=True)
+    assert rel_l2(S_g.cpu().numpy(), S_o) <= 1e-12
+    assert rel_l2(X_g.cpu().numpy(), X_o) <= 1e-12
+    rec32 = np.stack([rec.astype(np.float32), np.zeros_like(rec, dtype=np.float32)], -1)
+    S_k = lw.lw_spectrum(torch.from_numpy(rec32).cuda(), lw.LW_MIXED_KAHAN, n_pix, grid)
+    assert rel_l2(S_k.double().cpu().numpy(), S_o) <= 1e-5
+    S_m = lw.lw_spectrum(torch.from_numpy(rec).cuda(), lw.LW_MIXED, n_pix, grid)
+    assert rel_l2(S_m.double().cpu().numpy(), S_o) <= 1e-5
+
+
+def test_status_word_reports_bad_inputs():
+    tr = simple.stationary_constant_acceleration(20, 1e-18, (1e15, 0.0, 0.0))
+    n_hat = np.array([[0.0, 0.1, math.sqrt(1 - 0.01)]])
+    b = tr.beta.copy()
+    b[0, 3] = (0.0, 0.0, 1.0)
+    t = tr.t.copy()
+    t[7] = t[6]
+    bad = simple.Trajectories(t, tr.r, b, tr.beta_dot)
+    grid = lw.Grid(tr.t[0], 1e-18, 64)
+    for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN):
+        g = gpu_run(bad, n_hat, grid, prec, spectrum=False)
+        assert g["status"] & lw.LW_ST_BETA and g["status"] & lw.LW_ST_TIME

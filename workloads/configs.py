@@ -25,7 +25,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .boris import GaussianLaser, boris_trajectories, gaussian_bunch
+from .boris import GaussianLaser, gaussian_bunch
+from .parallel import boris_trajectories_parallel
 from .detector import detector_grid
 from .physics import C0, Q_E
 from .planewave import plane_wave_trajectories
@@ -84,7 +85,7 @@ def _c2_like(name, n_e, n_s, nx, n_bins, sigma_x, sigma_y, sigma_z, seed, half_a
         env = laser.sigma * np.sqrt(2.0 * np.log(1e6))
         t_half = 0.5 * (env + 4.0 * sigma_z / C0) * 1.05
     r0, u0 = gaussian_bunch(n_e, seed, sigma_x, sigma_y, sigma_z, gamma, spread, eps_n, -t_half)
-    tr = boris_trajectories(r0, u0, laser, -t_half, t_half, n_s)
+    tr = boris_trajectories_parallel(r0, u0, laser, -t_half, t_half, n_s)
     n_hat, tx, ty = detector_grid(nx, nx, half_angle_g / gamma)
     return Workload(name, tr, n_hat, n_bins, gamma=gamma, lam=laser.lam, a0=laser.a0,
                     theta_x=tx, theta_y=ty,
