@@ -351,6 +351,99 @@ def cpu_baseline(w, grid, S_gpu, args):
             "mixed_spectrum_rel_l2_vs_oracle_on_sample": err}
 
 
+# ----------------------------------------------------------------------------- C5 sweep
+
+def run_c5(args):
+    """Batched design sweep: all variants' deposits in one persistent launch and their
+    spectra, captured in one CUDA graph, against the same work launched variant by
+    variant; tile shapes from the autotuner."""
+    import torch
+
+    from paper_2206_03015_gb300 import lw
+    from paper_2206_03015_gb300.autotune import Autotuner
+    from workloads import configs
+
+    dev = torch.device("cuda", 0)
+    vs = configs.c5_batch(n_variants=args.c5_variants, n_e=(args.c5_ne[0], args.c5_ne[1]),
+                          n_s=(args.c5_ns[0], args.c5_ns[1]), nx=(args.c5_nx[0], args.c5_nx[1]),
+                          log2_bins=(args.c5_bins[0], args.c5_bins[1]))
+    t0 = time.time()
+    items = []
+    tuner = Autotuner(reps=1)
+    for v in vs:
+        w = v.build()
+        tr = w.traj
+        inputs = tuple(torch.from_numpy(x).to(dev) for x in (tr.t, tr.r, tr.beta, tr.beta_dot))
+        det = lw.Detector(w.n_hat, device=dev)
+        traj = lw.lw_trajectories_upload(*inputs, sections=lw.LW_SECTION_MIXED, device=dev)
+        b = lw.lw_grid_bounds(traj, det).cpu().numpy()
+        grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
+        choice = tuner.tune(inputs, det, grid, blocks=(64, 128, 256), chunks=(1, 2, 4, 8, 16))
+        traj = lw.lw_trajectories_upload(*inputs, sections=lw.LW_SECTION_MIXED,
+                                         block=choice.block, device=dev)
+        shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
+        rec = torch.empty(shp, dtype=dt, device=dev)
+        S = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float32, device=dev)
+        ws = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_MIXED, det.n_pix, grid), dev)
+        items.append(dict(w=w, traj=traj, det=det, grid=grid, rec=rec, S=S, ws=ws,
+                          choice=choice, deposits=w.deposits))
+        del inputs
+    t_setup = time.time() - t0
+    bp = lw.lw_batch_plan([i["traj"] for i in items], [i["det"] for i in items],
+                          [i["grid"] for i in items], [i["rec"] for i in items],
+                          e_chunks=[i["choice"].e_chunk for i in items])
+
+    def batched():
+        lw.lw_batch_deposit(bp)
+        for i in items:
+            lw.lw_spectrum(i["rec"], lw.LW_MIXED, i["det"].n_pix, i["grid"], ws=i["ws"],
+                           out=i["S"])
+
+    def sequential():
+        for i in items:
+            lw.lw_deposit_time_domain(i["traj"], i["det"], i["grid"], lw.LW_MIXED,
+                                      record=i["rec"])
+            lw.lw_spectrum(i["rec"], lw.LW_MIXED, i["det"].n_pix, i["grid"], ws=i["ws"],
+                           out=i["S"])
+
+    batched()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            batched()
+    torch.cuda.current_stream().wait_stream(st)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_graph = timed(g.replay)
+    ms_seq = timed(sequential)
+    dep = sum(i["deposits"] for i in items)
+    return {"metric": METRIC, "value": dep / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"c5 sweep: {len(items)} variants, one persistent deposit "
+                                   f"launch + spectra in one CUDA graph",
+                       "deposits_per_step": dep, "units": bp.plan.n_units,
+                       "setup_s": round(t_setup, 1),
+                       "tiles": [[i["choice"].block, i["choice"].e_chunk] for i in items]},
+            "sequential": {"value": dep / (ms_seq * 1e-3), "ms_per_step": ms_seq}}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -414,6 +507,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"])
+    ap.add_argument("--c5-variants", type=int, default=64)
+    ap.add_argument("--c5-ne", type=int, nargs=2, default=(128, 1024))
+    ap.add_argument("--c5-ns", type=int, nargs=2, default=(1000, 8000))
+    ap.add_argument("--c5-nx", type=int, nargs=2, default=(16, 64))
+    ap.add_argument("--c5-bins", type=int, nargs=2, default=(12, 16))
     args = ap.parse_args()
     args.full = (args.n_e, args.n_s, args.nx, args.n_bins) == (10_000, 10_000, 64, 65_536)
     world = _env_int("WORLD_SIZE", 1)
@@ -428,6 +527,8 @@ def main():
         dist = tdist
     if args.impl == "reference":
         res = run_reference(args, rank, world)
+    elif args.workload == "c5":
+        res = run_c5(args)
     else:
         res = run_ours(args, rank, world, dist)
     if rank == 0 and res is not None:

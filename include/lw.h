@@ -210,6 +210,105 @@ int lw_spectrum(const void* record, int32_t precision, int64_t n_pix, const lw_g
                 double q, void* spectrum, void* X_save, void* ws, size_t* ws_bytes,
                 void* stream);
 
+/* Adjoint of lw_deposit_time_domain followed by lw_spectrum (reverse-mode
+ * gradient of a loss L(S)).  Given g = dL/dS [n_pix][n_bins/2+1] (float64,
+ * device) and X_save written by lw_spectrum with LW_FP64, adds to
+ *   dL_dr, dL_dbeta, dL_dbeta_dot   float64 [n_e][n_s+1][3] (device, caller-zeroed)
+ * the gradient of L with respect to every sample's position, velocity and
+ * acceleration.  The record gradient is
+ *   dL/drec_c[j] = 2 sqrt(K) dt_u Re(sum_l g_l conj(X'_c(l)) exp(+2 pi i j l/N))
+ * (one complex FFT per two rows); the deposit is transposed as a gather over
+ * the same half-open intervals of Algorithm 2, differentiating the
+ * interpolation weights with respect to t_a and t_b, the advanced time
+ * (Eq. far_adv) with respect to r and the acceleration field (Eq. far_efield)
+ * with respect to beta and beta_dot.  L is piecewise smooth in the samples
+ * (grid points entering or leaving an interval change its slope but not its
+ * value); the result is the derivative on the current piece.
+ *   precision    LW_FP64 (the FP64 section must exist)
+ *   field_flags  LW_FIELD_ACCEL
+ *   q            particle charge [C] (as passed to lw_spectrum)
+ *   ws           device scratch (NULL = size query): dL/drec, twiddles and,
+ *                above 4096 bins, the four-step transform buffer
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (other precision/flags, n_bins not a power
+ * of two in [2, 2^18]), LW_ESIZE, LW_ECUDA. */
+int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, const lw_grid* grid,
+                     int32_t precision, uint32_t field_flags, const void* X_save,
+                     const double* dL_dS, double q, double* dL_dr, double* dL_dbeta,
+                     double* dL_dbeta_dot, void* ws, size_t* ws_bytes, void* stream);
+
+/* Frequency-domain method, Eq. (inty_dft) / Algorithm 1 (the paper's comparison
+ * method), on the uniform frequency grid omega_w = omega0 + w d_omega:
+ *   S[m][w] = q^2 dt^2 / (16 pi^3 eps0 c0)
+ *             |sum_k sum_{i=0}^{n_s} A_k(n_m, t_i) exp(j omega_w (t_i - n_m.r_ki/c0))|^2,
+ *   A = n x ((n - beta) x beta_dot) / (1 - n.beta)^2,
+ * with the same far-field phase time as lw_deposit_time_domain (|x|/c0 dropped)
+ * and the rectangle rule of weight dt over all stored samples.  Phase times,
+ * A and the phase reductions modulo 2 pi are FP64; twiddles and sums are
+ * double-FP32 / compensated FP32.  Needs the FP64 section.
+ *   spectrum  device float64 [n_pix][n_omega]
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (too many frequencies for one launch), LW_ECUDA. */
+int lw_spectrum_fdm(const lw_traj* traj, const lw_detector* det, double omega0, double d_omega,
+                    int64_t n_omega, double dt, double q, double* spectrum, void* stream);
+
+/* Laser of lw_boris_push: lowest-order paraxial Gaussian beam polarised along x,
+ * propagating along -z, focused at z = 0 and peaking there at t = 0. */
+typedef struct {
+    double lam;    /* wavelength [m] */
+    double a0;     /* normalised peak vector potential */
+    double w0;     /* waist [m] */
+    double fwhm;   /* intensity FWHM duration [s] */
+} lw_laser;
+
+/* Trajectory update of Algorithm 2 ("update trajectory", Boris method as in the
+ * paper's trial simulation) for the in-situ form of the path: advances n_e
+ * particles (r [n_e][3] in metres, u = gamma beta [n_e][3]; device, updated in
+ * place) by n_steps steps of dt from time t0 in the Gaussian laser, and writes
+ * the n_steps + 1 samples t_out [n_steps+1], r_out, beta_out, bdot_out
+ * [n_e][n_steps+1][3] (device, FP64) -- the layout of lw_traj_in -- including the
+ * starting state as sample 0, so consecutive calls overlap by one sample.
+ * Step: drift dt/2, Boris kick with the fields at the midpoint, drift dt/2;
+ * bdot = q/(m gamma c0) [E + c0 beta x B - beta (beta.E)] at each sample.
+ * Errors: LW_EINVAL, LW_ECUDA. */
+int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int32_t n_steps,
+                  const lw_laser* laser, double charge, double mass, double* t_out,
+                  double* r_out, double* beta_out, double* bdot_out, void* stream);
+
+/* Several independent problems ("variants": own trajectories, detector, grid
+ * and record) deposited by one persistent launch of the mixed-precision
+ * deposit (LW_MIXED or LW_MIXED_KAHAN).  The work is cut into units of
+ * (variant, 512-pixel tile, chunk of electrons) that resident CTAs take from a
+ * list, largest first, so variants of very different sizes share the GPU.
+ * Two calls:
+ *   lw_batch_plan     checks the items, writes the per-variant arguments and the
+ *                     work list into `ws` (NULL = size query) and fills `plan`;
+ *                     it copies from host memory and returns after the copies.
+ *   lw_batch_deposit  zeroes every record and launches the persistent kernel;
+ *                     it only enqueues stream-ordered work, so it can be
+ *                     repeated (and recorded in a CUDA graph) with the same plan.
+ * e_chunk (electrons per unit) comes from the item, or is chosen so that the
+ * batch splits into about eight units per resident CTA when it is 0.  Records
+ * and results are those of lw_deposit_time_domain for each variant.
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (LW_FP64), LW_ESIZE, LW_ECUDA. */
+typedef struct {
+    const lw_traj* traj;        /* uploaded with the mixed section */
+    const lw_detector* det;
+    lw_grid grid;
+    void* record;               /* 8 bytes per value, layout of lw_deposit_time_domain */
+    int32_t* status;            /* device int32 or NULL */
+    int32_t e_chunk;            /* electrons per work unit, 0 = automatic */
+} lw_batch_item;
+
+typedef struct {
+    void* ws;
+    int32_t n_items, n_units, precision, smem_bytes;
+    int64_t offsets[3];
+} lw_batch;
+
+int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_t precision,
+                  uint32_t field_flags, void* ws, size_t* ws_bytes, lw_batch* plan,
+                  void* stream);
+int lw_batch_deposit(const lw_batch* plan, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,9 @@
 // and contributions are added with a compensated pair of FP32 atomics.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "lw_internal.cuh"
 
 namespace lw {
@@ -247,15 +250,14 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __
 }
 
 // A step whose interval (t_b, t_a] contains grid points, recorded by the scan
-// loop of one lane and deposited later by the whole warp.
+// loop of one lane and deposited later by the whole warp (16 bytes).
 struct Event {
-    int slot;     // lane * PIX + q: pixel of the warp
-    int qq;       // step index within the staged block (sample i0 + qq)
-    int ja;       // first grid point (clipped)
-    int cnt;      // number of grid points
-    float a0;     // ja - u_{i-1}   [bins]
-    float du;     // u_i - u_{i-1}  [bins]
+    unsigned packed;   // slot (lane * PIX + q, 7 bits) | qq << 7 (10 bits) | cnt << 17 (15 bits)
+    int ja;            // first grid point (clipped)
+    float a0;          // ja - u_{i-1}   [bins]
+    float du;          // u_i - u_{i-1}  [bins]
 };
+constexpr int kMaxEventBins = (1 << 15) - 1;
 
 constexpr int kLaneQ = 8;                       // events per lane between drains
 constexpr int kWarps = kMixThreads / 32;
@@ -278,18 +280,27 @@ __device__ __forceinline__ int exact_bin(const double* e, double nx, double ny, 
     return (int)floor(u);
 }
 
+// Bin coordinate of a staged sample relative to the block anchor, without the
+// anchor fraction f: sc.x holds C = s*dtau + w_c . dr for the CTA's reference
+// slope w_c, dw = w_pixel - w_c, so u - I - f = C + dw . dr.
+template <int PIX>
+__device__ __forceinline__ float coord(const float (&dw)[PIX][3], int q, float4 sc) {
+    return fmaf(dw[q][2], sc.w, fmaf(dw[q][1], sc.z, fmaf(dw[q][0], sc.y, sc.x)));
+}
+
+// The work of one CTA: pixel tile `tile` (kMixThreads * PIX pixels) and electron
+// chunk `chunk` (p.e_chunk electrons) of one variant.  Returns the status bits.
 template <int PIX, bool KAHAN>
-__global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs p) {
+__device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     extern __shared__ float4 smem4[];
     const int B = p.block;
-    float4* s_scan = smem4;                                    // [B]
+    float4* s_scan = smem4;                                    // [B] (C, dx, dy, dz)
     float* s_field = reinterpret_cast<float*>(smem4 + B);      // [B+1][6], sample i0-1 first
     __shared__ float s_anch[8];                                // T, R_x, R_y, R_z (hi, lo)
+    __shared__ float s_wc[3];                                  // reference slope of the CTA
     __shared__ Event s_q[kWarps][kLaneQ * 32];                 // [warp][lane * kLaneQ + e]
     __shared__ int s_qn[kWarps][32];
-    __shared__ PixelConst s_pc[kMixThreads * PIX];
-    __shared__ int64_t s_pix[kMixThreads * PIX];
-    __shared__ float s_wl[kMixThreads * PIX][3];               // lo parts of the slopes
+    __shared__ float s_w[kMixThreads * PIX][6];                // slopes: hi parts, lo parts
     __shared__ int s_jlast[kMixThreads * PIX];                 // exact bin of the last sample
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -297,13 +308,14 @@ __global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs 
     const float s32 = (float)p.inv_dtu;
     const float c0_over_R = (float)(kC0 / p.R);
     const int nb = (int)p.n_bins;
-    float wh[PIX][3];
-    bool act[PIX];
+    const int64_t pix0 = tile * kMixThreads * PIX;
+    unsigned act = 0;
+    __syncthreads();   // shared arrays may still be read by the previous unit
     for (int q = 0; q < PIX; ++q) {
-        const int64_t m = (int64_t)blockIdx.x * kMixThreads * PIX + q * kMixThreads + threadIdx.x;
-        act[q] = m < p.n_pix;
+        const int64_t m = pix0 + q * kMixThreads + threadIdx.x;
         double nx = 0.0, ny = 0.0, nz = 1.0;
-        if (act[q]) {
+        if (m < p.n_pix) {
+            act |= 1u << q;
             nx = p.n_hat[3 * m];
             ny = p.n_hat[3 * m + 1];
             nz = p.n_hat[3 * m + 2];
@@ -312,50 +324,104 @@ __global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs 
         const double sc = kInvC0 * p.inv_dtu;
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
-        wh[q][0] = wx.hi;
-        wh[q][1] = wy.hi;
-        wh[q][2] = wz.hi;
-        const int slot = wslot + lane * PIX + q;
-        s_wl[slot][0] = wx.lo;
-        s_wl[slot][1] = wy.lo;
-        s_wl[slot][2] = wz.lo;
-        s_pc[slot] = PixelConst{(float)nx, (float)ny, (float)nz, (float)omnz};
-        s_pix[slot] = act[q] ? m : 0;
+        float* w = s_w[wslot + lane * PIX + q];
+        w[0] = wx.hi;
+        w[1] = wy.hi;
+        w[2] = wz.hi;
+        w[3] = wx.lo;
+        w[4] = wy.lo;
+        w[5] = wz.lo;
+        if (threadIdx.x == 0 && q == 0) {
+            s_wc[0] = wx.hi;
+            s_wc[1] = wy.hi;
+            s_wc[2] = wz.hi;
+        }
     }
+    __syncthreads();
+    float dw[PIX][3];
+    for (int q = 0; q < PIX; ++q)
+        for (int c = 0; c < 3; ++c) dw[q][c] = s_w[wslot + lane * PIX + q][c] - s_wc[c];
+    const float wcx = s_wc[0], wcy = s_wc[1], wcz = s_wc[2];
     Event* myq = s_q[warp] + lane * kLaneQ;
     int* qn = s_qn[warp];
     int nq = 0;                                  // this lane's queued events
     int bits = 0;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.input_status)
-        bits |= *p.input_status;
+    if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
 
-    const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
+    // pixel (global index) of warp slot `sl`
+    auto slot_pixel = [&](int sl) -> int64_t {
+        const int ln = sl / PIX, q = sl % PIX;
+        return pix0 + q * kMixThreads + warp * 32 + ln;
+    };
+    // deposit the grid points [ja, ja+cnt) of one crossing of pixel `m`
+    auto deposit = [&](int64_t m, int qq, int ja, int cnt, float a0, float du) {
+        const double* nh = p.n_hat + 3 * m;
+        PixelConst pc;
+        pc.nx = (float)nh[0];
+        pc.ny = (float)nh[1];
+        pc.nz = (float)nh[2];
+        pc.omnz = (pc.nx * pc.nx + pc.ny * pc.ny) / (1.0f + pc.nz);   // no cancellation
+        const int64_t base = m * 3 * p.n_bins;
+        float Fb[3], Fa[3];
+        field_fp32(pc, s_field + 6 * qq, p.flags, c0_over_R, Fb);
+        field_fp32(pc, s_field + 6 * (qq + 1), p.flags, c0_over_R, Fa);
+        const float inv_du = du > 0.0f ? 1.0f / du : 0.0f;
+        for (int t = 0; t < cnt; ++t) {
+            const float wb = (a0 + (float)t) * inv_du;
+            const float wa = 1.0f - wb;
+            const int64_t j = base + ja + t;
+            accumulate<KAHAN>(p.record, j, fmaf(Fb[0], wa, Fa[0] * wb));
+            accumulate<KAHAN>(p.record, j + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+            accumulate<KAHAN>(p.record, j + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+        }
+    };
+    // deposit every queued event of the warp with all 32 lanes
+    auto drain = [&]() {
+        qn[lane] = nq;
+        __syncwarp();
+        for (int e = lane; e < 32 * kLaneQ; e += 32) {
+            const int owner = e / kLaneQ, idx = e % kLaneQ;
+            if (idx >= qn[owner]) continue;
+            const Event ev = s_q[warp][owner * kLaneQ + idx];
+            deposit(slot_pixel((int)(ev.packed & 127u)), (int)((ev.packed >> 7) & 1023u), ev.ja,
+                    (int)(ev.packed >> 17), ev.a0, ev.du);
+        }
+        __syncwarp();
+        nq = 0;
+    };
+
+    const int64_t k0 = chunk * p.e_chunk;
     const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
     for (int64_t k = k0; k < k1; ++k) {
         const float4* sck = p.scan + k * p.ns1;
         const float* fdk = p.field + 6 * k * p.ns1;
         const D4* anc = p.anchor + k * p.n_blocks;
         const double* ends = p.ends + 8 * k;
-        // per pixel: I = integer anchor of the block, thr = floor(u_{i-1}) + 1 - I (the
-        // next grid point relative to the anchor), vprev = u_{i-1} - I, f = U_b - I
+        // per pixel: I = integer anchor of the block, f = U_b - I, thr = next grid point
+        // relative to I (floor(u_{i-1}) + 1 - I), tr = thr - f (threshold for the
+        // coordinate without f), vlast = coordinate (with f) of the block's last sample
         int I[PIX];
-        float vprev[PIX], thr[PIX], f[PIX];
+        float thr[PIX], f[PIX], tr[PIX], vlast[PIX];
         for (int q = 0; q < PIX; ++q) {
             // exact bins of the first and last samples: the half-open interval of
             // Algorithm 2 makes these the only samples where a one-bin rounding flip
             // changes the record by a whole sample
-            const int64_t m = s_pix[wslot + lane * PIX + q];
+            const int64_t m = (act >> q & 1u) ? pix0 + q * kMixThreads + threadIdx.x : 0;
             const double nx = p.n_hat[3 * m], ny = p.n_hat[3 * m + 1], nz = p.n_hat[3 * m + 2];
             thr[q] = (float)(exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu) + 1);
             s_jlast[wslot + lane * PIX + q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
             I[q] = 0;
-            vprev[q] = 0.0f;
+            vlast[q] = 0.0f;
         }
         for (int b = 0; b < p.n_blocks; ++b) {
             const int64_t i0 = (int64_t)b * B;
             const int n = (int)min((int64_t)B, p.ns1 - i0);
             __syncthreads();
-            for (int q = threadIdx.x; q < n; q += kMixThreads) s_scan[q] = sck[i0 + q];
+            for (int q = threadIdx.x; q < n; q += kMixThreads) {
+                float4 v = sck[i0 + q];
+                v.x = fmaf(wcz, v.w, fmaf(wcy, v.z, fmaf(wcx, v.y, s32 * v.x)));
+                s_scan[q] = v;
+            }
             for (int q = threadIdx.x; q < 6 * (n + 1); q += kMixThreads) {
                 const int64_t idx = 6 * (i0 - 1) + q;
                 s_field[q] = (idx >= 0) ? fdk[idx] : 0.0f;
@@ -374,17 +440,18 @@ __global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs 
                 s_anch[7] = Z.lo;
             }
             __syncthreads();
+            float v0p[PIX];   // coordinate (with f) of sample i0-1 relative to this anchor
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
                 // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
-                const float* wlq = s_wl[wslot + lane * PIX + q];
+                const float* w = s_w[wslot + lane * PIX + q];
                 float s = s_anch[0], e = s_anch[1];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const float Rh = s_anch[2 + 2 * c], Rl = s_anch[3 + 2 * c];
-                    const float pr = __fmul_rn(wh[q][c], Rh);
-                    float pe = fmaf(wh[q][c], Rh, -pr);
-                    pe = fmaf(wh[q][c], Rl, fmaf(wlq[c], Rh, pe));
+                    const float pr = __fmul_rn(w[c], Rh);
+                    float pe = fmaf(w[c], Rh, -pr);
+                    pe = fmaf(w[c], Rl, fmaf(w[3 + c], Rh, pe));
                     const float s2 = __fadd_rn(s, pr);
                     const float bb = __fsub_rn(s2, s);
                     const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)),
@@ -396,94 +463,135 @@ __global__ void __launch_bounds__(kMixThreads) deposit_mixed_kernel(DepositArgs 
                 const float Is = floorf(s);
                 const int Inew = (int)Is;
                 f[q] = __fadd_rn(__fsub_rn(s, Is), e);
-                vprev[q] = __fadd_rn(vprev[q], (float)(I[q] - Inew));   // rebase sample i-1
-                thr[q] = act[q] ? thr[q] + (float)(I[q] - Inew) : INFINITY;
+                v0p[q] = __fadd_rn(vlast[q], (float)(I[q] - Inew));   // rebase sample i0-1
+                thr[q] = (act >> q & 1u) ? thr[q] + (float)(I[q] - Inew) : INFINITY;
+                tr[q] = thr[q] - f[q];
                 I[q] = Inew;
             }
-            int qq = 0;
-            if (b == 0) {   // the first sample only fills the buffer of Algorithm 2
-                const float4 sc = s_scan[0];
-#pragma unroll
-                for (int q = 0; q < PIX; ++q)
-                    vprev[q] = fmaf(wh[q][2], sc.w,
-                                    fmaf(wh[q][1], sc.z, fmaf(wh[q][0], sc.y,
-                                                              fmaf(s32, sc.x, f[q]))));
-                qq = 1;
-            }
+            // record a crossing of pixel q at staged step qq (coordinate v, previous vp)
+            auto cross = [&](int q, int qq, float v, float vp, int jnew) {
+                int ja = (int)thr[q] + I[q], jz = jnew;
+                if (ja < 0) {
+                    ja = 0;
+                    bits |= LW_ST_CLIP;
+                }
+                if (jz > nb - 1) {
+                    jz = nb - 1;
+                    bits |= LW_ST_CLIP;
+                }
+                if (ja <= jz) {
+                    const int cnt = jz - ja + 1;
+                    const float a0 = __fsub_rn((float)(ja - I[q]), vp);
+                    const float du = __fsub_rn(v, vp);
+                    if (cnt <= kMaxEventBins) {
+                        Event ev;
+                        ev.packed = (unsigned)(lane * PIX + q) | ((unsigned)qq << 7) |
+                                    ((unsigned)cnt << 17);
+                        ev.ja = ja;
+                        ev.a0 = a0;
+                        ev.du = du;
+                        myq[nq++] = ev;
+                    } else {   // a step spanning more grid points than an event holds
+                        deposit(pix0 + q * kMixThreads + threadIdx.x, qq, ja, cnt, a0, du);
+                    }
+                }
+                thr[q] = (float)(jnew + 1 - I[q]);
+                tr[q] = thr[q] - f[q];
+            };
             const bool last_block = (i0 + n == p.ns1);
+            const int qend = last_block ? n - 1 : n;   // the last sample is peeled below
+            int qq = (b == 0) ? 1 : 0;                  // sample 0 only fills the buffer
             while (true) {
-                // scan until the block ends or some lane's queue could overflow
-                for (; qq < n; ++qq) {
+                for (; qq < qend; ++qq) {
                     if (__any_sync(0xffffffffu, nq > kLaneQ - PIX)) break;
                     const float4 sc = s_scan[qq];
-                    const bool is_last = last_block && qq == n - 1;
+                    float v[PIX];
+                    bool any = false;
 #pragma unroll
                     for (int q = 0; q < PIX; ++q) {
-                        const float v = fmaf(wh[q][2], sc.w,
-                                             fmaf(wh[q][1], sc.z,
-                                                  fmaf(wh[q][0], sc.y, fmaf(s32, sc.x, f[q]))));
-                        bool cross = v >= thr[q];
-                        int jnew = 0;
-                        if (is_last) {   // exact bin of the last sample
-                            jnew = s_jlast[wslot + lane * PIX + q];
-                            cross = act[q] && jnew + 1 - I[q] > (int)thr[q];
+                        v[q] = coord<PIX>(dw, q, sc);
+                        any |= v[q] >= tr[q];
+                    }
+                    if (any) {
+                        const float4 sp = s_scan[qq > 0 ? qq - 1 : 0];
+#pragma unroll
+                        for (int q = 0; q < PIX; ++q) {
+                            if (v[q] >= tr[q]) {
+                                const float vf = v[q] + f[q];
+                                const float vp = qq > 0 ? coord<PIX>(dw, q, sp) + f[q] : v0p[q];
+                                cross(q, qq, vf, vp, I[q] + (int)floorf(vf));
+                            }
                         }
-                        if (cross) {
-                            if (!is_last) jnew = I[q] + (int)floorf(v);
-                            int ja = (int)thr[q] + I[q], jz = jnew;
-                            if (ja < 0) {
-                                ja = 0;
-                                bits |= LW_ST_CLIP;
-                            }
-                            if (jz > nb - 1) {
-                                jz = nb - 1;
-                                bits |= LW_ST_CLIP;
-                            }
-                            if (ja <= jz) {
-                                Event ev;
-                                ev.slot = lane * PIX + q;
-                                ev.qq = qq;
-                                ev.ja = ja;
-                                ev.cnt = jz - ja + 1;
-                                ev.a0 = __fsub_rn((float)(ja - I[q]), vprev[q]);
-                                ev.du = __fsub_rn(v, vprev[q]);
-                                myq[nq++] = ev;
-                            }
-                            thr[q] = (float)(jnew + 1 - I[q]);
-                        }
-                        vprev[q] = v;
                     }
                 }
-                // deposit the queued events with all lanes of the warp
-                qn[lane] = nq;
-                __syncwarp();
-                for (int e = lane; e < 32 * kLaneQ; e += 32) {
-                    const int owner = e / kLaneQ, idx = e % kLaneQ;
-                    if (idx >= qn[owner]) continue;
-                    const Event ev = s_q[warp][owner * kLaneQ + idx];
-                    const PixelConst pc = s_pc[wslot + ev.slot];
-                    const int64_t base = s_pix[wslot + ev.slot] * 3 * p.n_bins;
-                    float Fb[3], Fa[3];
-                    field_fp32(pc, s_field + 6 * ev.qq, p.flags, c0_over_R, Fb);
-                    field_fp32(pc, s_field + 6 * (ev.qq + 1), p.flags, c0_over_R, Fa);
-                    const float inv_du = ev.du > 0.0f ? 1.0f / ev.du : 0.0f;
-                    for (int t = 0; t < ev.cnt; ++t) {
-                        const float wb = (ev.a0 + (float)t) * inv_du;
-                        const float wa = 1.0f - wb;
-                        const int64_t j = base + ev.ja + t;
-                        accumulate<KAHAN>(p.record, j, fmaf(Fb[0], wa, Fa[0] * wb));
-                        accumulate<KAHAN>(p.record, j + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-                        accumulate<KAHAN>(p.record, j + 2 * p.n_bins,
-                                          fmaf(Fb[2], wa, Fa[2] * wb));
+                drain();
+                if (qq >= qend) break;
+            }
+            if (last_block) {   // exact bin of the last sample (queue is empty here)
+                const int qq = n - 1;
+                const float4 sc = s_scan[qq];
+                const float4 sp = s_scan[qq > 0 ? qq - 1 : 0];
+#pragma unroll
+                for (int q = 0; q < PIX; ++q) {
+                    const int jl = s_jlast[wslot + lane * PIX + q];
+                    if ((act >> q & 1u) && jl + 1 - I[q] > (int)thr[q]) {
+                        const float v = coord<PIX>(dw, q, sc) + f[q];
+                        const float vp = qq > 0 ? coord<PIX>(dw, q, sp) + f[q] : v0p[q];
+                        cross(q, qq, v, vp, jl);
                     }
                 }
-                __syncwarp();
-                nq = 0;
-                if (qq >= n) break;
+                drain();
+            } else {
+                const float4 sc = s_scan[n - 1];
+#pragma unroll
+                for (int q = 0; q < PIX; ++q) vlast[q] = coord<PIX>(dw, q, sc) + f[q];
             }
         }
     }
+    return bits;
+}
+
+template <int PIX, bool KAHAN>
+__global__ void __launch_bounds__(kMixThreads, 5) deposit_mixed_kernel(DepositArgs p) {
+    const int bits = mixed_cta<PIX, KAHAN>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
+}
+
+// Persistent form: CTAs pull (variant, pixel tile, electron chunk) units from a
+// list in decreasing order of work until the list is exhausted.
+struct BatchUnit {
+    int variant;
+    int tile;
+    int chunk;
+    int pad;
+};
+
+template <int PIX, bool KAHAN>
+__global__ void __launch_bounds__(kMixThreads, 5)
+    deposit_batched_kernel(const DepositArgs* __restrict__ vars,
+                           const BatchUnit* __restrict__ units, int n_units, int* counter) {
+    __shared__ int s_unit;
+    while (true) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= n_units) break;
+        const BatchUnit un = units[u];
+        const DepositArgs p = vars[un.variant];
+        const int bits = mixed_cta<PIX, KAHAN>(p, un.tile, un.chunk);
+        block_status_or(p.status, bits);
+    }
+}
+
+__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int n_vars) {
+    for (int v = 0; v < n_vars; ++v) {
+        double* rec = static_cast<double*>(vars[v].record);   // 8-byte values in every precision
+        const int64_t n = vars[v].n_pix * 3 * vars[v].n_bins;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            rec[i] = 0.0;
+    }
 }
 
 int pick_chunk(int64_t n_e, int64_t tiles) {
@@ -558,9 +666,171 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     a.e_chunk = pick_chunk(traj->n_e, tiles);
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
     const size_t smem = sizeof(float4) * traj->block + sizeof(float) * 6 * (traj->block + 1);
-    if (precision == LW_MIXED_KAHAN)
-        deposit_mixed_kernel<PIX, true><<<g, kMixThreads, smem, st>>>(a);
-    else
-        deposit_mixed_kernel<PIX, false><<<g, kMixThreads, smem, st>>>(a);
+    // static queues + dynamic staging exceed the 48 KB default: opt in
+    auto kern = precision == LW_MIXED_KAHAN ? deposit_mixed_kernel<PIX, true>
+                                            : deposit_mixed_kernel<PIX, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return LW_ECUDA;
+    kern<<<g, kMixThreads, smem, st>>>(a);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: several independent problems in one persistent launch.
+namespace lw {
+namespace {
+
+struct BatchHeader {
+    int n_items, n_units, precision, smem;
+};
+
+size_t batch_layout(int n_items, int64_t n_units, size_t* off_vars, size_t* off_units,
+                    size_t* off_counter) {
+    size_t off = 0;
+    *off_counter = off;
+    off = align256(off + sizeof(int));
+    *off_vars = off;
+    off = align256(off + sizeof(DepositArgs) * (size_t)n_items);
+    *off_units = off;
+    off = align256(off + sizeof(BatchUnit) * (size_t)n_units);
+    return off;
+}
+
+}  // namespace
+}  // namespace lw
+
+extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_t precision,
+                             uint32_t field_flags, void* ws, size_t* ws_bytes, lw_batch* plan,
+                             void* stream) {
+    constexpr int PIX = 4;
+    if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
+    if (precision != LW_MIXED && precision != LW_MIXED_KAHAN) return LW_EUNSUPPORTED;
+    if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
+    std::vector<DepositArgs> vars((size_t)n_items);
+    std::vector<BatchUnit> units;
+    std::vector<int64_t> unit_work;
+    int max_block = 16;
+    int64_t total = 0;
+    const int64_t px_per_cta = (int64_t)kMixThreads * PIX;
+    for (int v = 0; v < n_items; ++v) {
+        const lw_batch_item& it = items[v];
+        if (!it.traj || !it.det || !it.record || !it.det->n_hat || it.det->n_pix < 1) return LW_EINVAL;
+        if (!(it.traj->sections & LW_SECTION_MIXED)) return LW_EINVAL;
+        if (it.grid.n_bins < 1 || it.grid.n_bins > (int64_t(1) << 30)) return LW_EINVAL;
+        if (!(it.grid.dt_u > 0.0) || !isfinite(it.grid.dt_u) || !isfinite(it.grid.t_min))
+            return LW_EINVAL;
+        if ((field_flags & LW_FIELD_VELOCITY) && !(it.det->R > 0.0)) return LW_EINVAL;
+        total += it.traj->n_e * it.traj->n_s * it.det->n_pix;
+        if (it.traj->block > max_block) max_block = it.traj->block;
+    }
+    // unit size: aim at ~8 units per resident CTA over the whole batch
+    const int64_t target = total / ((int64_t)kSms * 5 * 8) + 1;
+    for (int v = 0; v < n_items; ++v) {
+        const lw_batch_item& it = items[v];
+        DepositArgs& a = vars[(size_t)v];
+        a = DepositArgs{};
+        a.n_e = it.traj->n_e;
+        a.ns1 = it.traj->n_s + 1;
+        a.t_per_e = it.traj->t_per_electron;
+        a.scan = static_cast<const float4*>(it.traj->scan);
+        a.field = static_cast<const float*>(it.traj->field);
+        a.anchor = reinterpret_cast<const D4*>(it.traj->anchor);
+        a.block = it.traj->block;
+        a.n_blocks = it.traj->n_blocks;
+        a.input_status = it.traj->input_status;
+        a.ends = it.traj->ends;
+        a.n_hat = it.det->n_hat;
+        a.n_pix = it.det->n_pix;
+        a.R = it.det->R > 0.0 ? it.det->R : 1.0;
+        a.t_min = it.grid.t_min;
+        a.dt_u = it.grid.dt_u;
+        a.inv_dtu = 1.0 / it.grid.dt_u;
+        a.n_bins = it.grid.n_bins;
+        a.flags = field_flags;
+        a.record = it.record;
+        a.status = it.status;
+        const int64_t tiles = (a.n_pix + px_per_cta - 1) / px_per_cta;
+        int64_t chunk = it.e_chunk;
+        if (chunk <= 0) {
+            chunk = target / (px_per_cta * it.traj->n_s);
+            if (chunk < 1) chunk = 1;
+        }
+        if (chunk > a.n_e) chunk = a.n_e;
+        a.e_chunk = (int)chunk;
+        const int64_t chunks = (a.n_e + chunk - 1) / chunk;
+        for (int64_t c = 0; c < chunks; ++c)
+            for (int64_t t = 0; t < tiles; ++t) {
+                units.push_back(BatchUnit{v, (int)t, (int)c, 0});
+                const int64_t ne = std::min(chunk, a.n_e - c * chunk);
+                const int64_t np = std::min(px_per_cta, a.n_pix - t * px_per_cta);
+                unit_work.push_back(ne * it.traj->n_s * np);
+            }
+    }
+    // largest units first
+    std::vector<size_t> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return unit_work[x] > unit_work[y]; });
+    std::vector<BatchUnit> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    size_t o_vars, o_units, o_counter;
+    const size_t need = batch_layout(n_items, (int64_t)sorted.size(), &o_vars, &o_units, &o_counter);
+    if (!ws) {
+        *ws_bytes = need;
+        return LW_OK;
+    }
+    if (*ws_bytes < need) {
+        *ws_bytes = need;
+        return LW_ESIZE;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    char* base = static_cast<char*>(ws);
+    if (cudaMemcpyAsync(base + o_vars, vars.data(), sizeof(DepositArgs) * vars.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(base + o_units, sorted.data(), sizeof(BatchUnit) * sorted.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return LW_ECUDA;
+    // pageable sources: make sure the copies have consumed them before returning
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LW_ECUDA;
+    plan->ws = ws;
+    plan->n_items = n_items;
+    plan->n_units = (int32_t)sorted.size();
+    plan->precision = precision;
+    plan->smem_bytes = (int32_t)(sizeof(float4) * max_block + sizeof(float) * 6 * (max_block + 1));
+    plan->offsets[0] = (int64_t)o_counter;
+    plan->offsets[1] = (int64_t)o_vars;
+    plan->offsets[2] = (int64_t)o_units;
+    *ws_bytes = need;
+    return LW_OK;
+}
+
+extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
+    constexpr int PIX = 4;
+    if (!plan || !plan->ws || plan->n_items < 1) return LW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    char* base = static_cast<char*>(plan->ws);
+    int* counter = reinterpret_cast<int*>(base + plan->offsets[0]);
+    const DepositArgs* vars = reinterpret_cast<const DepositArgs*>(base + plan->offsets[1]);
+    const BatchUnit* units = reinterpret_cast<const BatchUnit*>(base + plan->offsets[2]);
+    zero_records_kernel<<<kSms * 8, 256, 0, st>>>(vars, plan->n_items);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return LW_ECUDA;
+    auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, true>
+                                                  : deposit_batched_kernel<PIX, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             plan->smem_bytes) != cudaSuccess)
+        return LW_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMixThreads,
+                                                      plan->smem_bytes) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int dev = 0, sms = kSms;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(plan->n_units, sms * per_sm);
+    kern<<<grid, kMixThreads, plan->smem_bytes, st>>>(vars, units, plan->n_units, counter);
     return launch_status();
 }

@@ -53,6 +53,12 @@ class lw_traj(ctypes.Structure):
                 ("ends", ctypes.c_void_p), ("input_status", ctypes.c_void_p)]
 
 
+class lw_batch(ctypes.Structure):
+    _fields_ = [("ws", ctypes.c_void_p), ("n_items", ctypes.c_int32), ("n_units", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("offsets", ctypes.c_int64 * 3)]
+
+
 class lw_detector(ctypes.Structure):
     _fields_ = [("n_pix", ctypes.c_int64), ("n_hat", ctypes.c_void_p), ("R", ctypes.c_double)]
 
@@ -62,10 +68,23 @@ class lw_grid(ctypes.Structure):
                 ("n_bins", ctypes.c_int64)]
 
 
+class lw_laser(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
+                ("fwhm", ctypes.c_double)]
+
+
+class lw_batch_item(ctypes.Structure):
+    _fields_ = [("traj", ctypes.c_void_p), ("det", ctypes.c_void_p), ("grid", lw_grid),
+                ("record", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("e_chunk", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain", "lw_spectrum")
+EXPORTS = ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain", "lw_spectrum",
+           "lw_spectrum_grad", "lw_batch_plan", "lw_batch_deposit",
+           "lw_spectrum_fdm", "lw_boris_push")
 
 
 def library_path() -> str:
@@ -94,6 +113,21 @@ def load(build_if_missing: bool = True):
                                                ctypes.c_uint32, P, ctypes.c_int32, P, P]
         lib.lw_spectrum.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(lw_grid),
                                     ctypes.c_double, P, P, P, ctypes.POINTER(ctypes.c_size_t), P]
+        lib.lw_spectrum_grad.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector),
+                                         ctypes.POINTER(lw_grid), ctypes.c_int32, ctypes.c_uint32,
+                                         P, P, ctypes.c_double, P, P, P, P,
+                                         ctypes.POINTER(ctypes.c_size_t), P]
+        lib.lw_boris_push.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int32, ctypes.POINTER(lw_laser), ctypes.c_double,
+                                      ctypes.c_double, P, P, P, P, P]
+        lib.lw_spectrum_fdm.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector),
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_double, P, P]
+        lib.lw_batch_plan.argtypes = [ctypes.POINTER(lw_batch_item), ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_uint32, P,
+                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(lw_batch),
+                                      P]
+        lib.lw_batch_deposit.argtypes = [ctypes.POINTER(lw_batch), P]
         for f in EXPORTS:
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -295,3 +329,106 @@ def lw_spectrum(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E, 
     if want_X:
         return S, torch.view_as_complex(X)
     return S
+
+
+def lw_spectrum_grad(traj: Trajectories, det: Detector, grid: Grid, X_save, dL_dS,
+                     q: float = Q_E, out=None, field_flags: int = LW_FIELD_ACCEL):
+    """Adjoint of deposit + spectrum (FP64).  X_save: complex128 [n_pix][3][n_bins/2+1]
+    from lw_spectrum(..., want_X=True); dL_dS: float64 [n_pix][n_bins/2+1].
+    Returns (dL/dr, dL/dbeta, dL/dbeta_dot), each float64 [n_e][n_s+1][3]
+    (added to ``out`` when given)."""
+    lib = load()
+    dev = det.n_hat.device
+    shape = (traj.n_e, traj.n_s + 1, 3)
+    if out is None:
+        out = tuple(torch.zeros(shape, dtype=torch.float64, device=dev) for _ in range(3))
+    X = torch.view_as_real(X_save.contiguous()) if X_save.is_complex() else X_save.contiguous()
+    assert X.dtype == torch.float64
+    g = dL_dS.to(torch.float64).contiguous()
+    d = det.c()
+    gr = grid.c()
+    nbytes = ctypes.c_size_t(0)
+    _check("lw_spectrum_grad", lib.lw_spectrum_grad(ctypes.byref(traj.view), ctypes.byref(d),
+                                                    ctypes.byref(gr), LW_FP64, field_flags, None,
+                                                    None, q, None, None, None, None,
+                                                    ctypes.byref(nbytes), None))
+    ws = _aligned_bytes(nbytes.value, dev)
+    _check("lw_spectrum_grad", lib.lw_spectrum_grad(ctypes.byref(traj.view), ctypes.byref(d),
+                                                    ctypes.byref(gr), LW_FP64, field_flags,
+                                                    _ptr(X), _ptr(g), q, _ptr(out[0]),
+                                                    _ptr(out[1]), _ptr(out[2]), _ptr(ws),
+                                                    ctypes.byref(nbytes), _stream()))
+    return out
+
+
+class BatchPlan:
+    """A planned batched deposit (see lw_batch_plan in lw.h); keeps everything the
+    device plan points to alive."""
+
+    def __init__(self, ws, plan, keep):
+        self.ws = ws
+        self.plan = plan
+        self._keep = keep
+
+
+def lw_batch_plan(trajs, dets, grids, records, precision=LW_MIXED, field_flags=LW_FIELD_ACCEL,
+                  statuses=None, e_chunks=None) -> BatchPlan:
+    """Plan one persistent launch over several variants (lists of equal length)."""
+    lib = load()
+    n = len(trajs)
+    items = (lw_batch_item * n)()
+    dets_c = [d.c() for d in dets]
+    for v in range(n):
+        items[v].traj = ctypes.addressof(trajs[v].view)
+        items[v].det = ctypes.addressof(dets_c[v])
+        items[v].grid = grids[v].c()
+        items[v].record = records[v].data_ptr()
+        items[v].status = statuses[v].data_ptr() if statuses is not None else None
+        items[v].e_chunk = int(e_chunks[v]) if e_chunks is not None else 0
+    nbytes = ctypes.c_size_t(0)
+    plan = lw_batch()
+    _check("lw_batch_plan", lib.lw_batch_plan(items, n, precision, field_flags, None,
+                                              ctypes.byref(nbytes), ctypes.byref(plan), None))
+    dev = dets[0].n_hat.device
+    ws = _aligned_bytes(nbytes.value, dev)
+    _check("lw_batch_plan", lib.lw_batch_plan(items, n, precision, field_flags, _ptr(ws),
+                                              ctypes.byref(nbytes), ctypes.byref(plan),
+                                              _stream()))
+    return BatchPlan(ws, plan, (trajs, dets, dets_c, records, statuses))
+
+
+def lw_batch_deposit(bp: BatchPlan):
+    """Zero the records and run the persistent deposit on the current stream."""
+    lib = load()
+    _check("lw_batch_deposit", lib.lw_batch_deposit(ctypes.byref(bp.plan), _stream()))
+
+
+def lw_spectrum_fdm(traj: Trajectories, det: Detector, omega0: float, d_omega: float,
+                    n_omega: int, dt: float, q: float = Q_E, out=None):
+    """Frequency-domain method (Eq. inty_dft) on omega_w = omega0 + w d_omega; float64
+    [n_pix][n_omega]."""
+    lib = load()
+    S = out if out is not None else torch.empty((det.n_pix, int(n_omega)), dtype=torch.float64,
+                                                device=det.n_hat.device)
+    d = det.c()
+    _check("lw_spectrum_fdm", lib.lw_spectrum_fdm(ctypes.byref(traj.view), ctypes.byref(d),
+                                                  float(omega0), float(d_omega), int(n_omega),
+                                                  float(dt), float(q), _ptr(S), _stream()))
+    return S
+
+
+M_E = 9.1093837015e-31
+
+
+def lw_boris_push(r, u, t0: float, dt: float, n_steps: int, laser, t_out, r_out, beta_out,
+                  bdot_out, charge: float = -Q_E, mass: float = M_E):
+    """Advance (r, u) [n_e, 3] (float64 CUDA tensors, in place) by n_steps Boris steps in the
+    Gaussian laser (lam, a0, w0, fwhm) and write the n_steps+1 samples into the outputs
+    (t_out [n_steps+1], r_out/beta_out/bdot_out [n_e, n_steps+1, 3])."""
+    lib = load()
+    L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
+    _check("lw_boris_push", lib.lw_boris_push(_ptr(r), _ptr(u), r.shape[0], float(t0),
+                                              float(dt), int(n_steps), ctypes.byref(L),
+                                              float(charge), float(mass), _ptr(t_out),
+                                              _ptr(r_out), _ptr(beta_out), _ptr(bdot_out),
+                                              _stream()))

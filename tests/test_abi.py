@@ -19,7 +19,7 @@ def declared_functions():
         if h.endswith(".h"):
             with open(os.path.join(ROOT, "include", h)) as f:
                 text = f.read()
-            names += re.findall(r"^int\s+(lw_\w+)\s*\(", text, flags=re.M)
+            names += re.findall(r"^(?:int|size_t)\s+(lw_\w+)\s*\(", text, flags=re.M)
     return names
 
 
@@ -95,3 +95,31 @@ def test_spectrum_size_query_and_limits(lib):
         g = lw.lw_grid(0.0, 1e-18, n)
         assert lib.lw_spectrum(None, lw.LW_FP64, 10, ctypes.byref(g), 1.6e-19, None, None, None,
                                ctypes.byref(nbytes), None) == lw.LW_EUNSUPPORTED
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the C sizes and field offsets."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "lw.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lw_traj_in), sizeof(lw_traj), sizeof(lw_detector),
+         sizeof(lw_grid), sizeof(lw_batch_item), sizeof(lw_batch));
+  printf("%zu %zu %zu %zu\n", offsetof(lw_traj, t), offsetof(lw_traj, input_status),
+         offsetof(lw_batch_item, grid), offsetof(lw_batch_item, e_chunk));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    sizes = [int(x) for x in out[:6]]
+    offs = [int(x) for x in out[6:]]
+    assert sizes == [ctypes.sizeof(c) for c in (lw.lw_traj_in, lw.lw_traj, lw.lw_detector,
+                                                lw.lw_grid, lw.lw_batch_item, lw.lw_batch)]
+    assert offs == [lw.lw_traj.t.offset, lw.lw_traj.input_status.offset,
+                    lw.lw_batch_item.grid.offset, lw.lw_batch_item.e_chunk.offset]

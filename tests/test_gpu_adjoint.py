@@ -1,0 +1,135 @@
+"""Adjoint (lw_spectrum_grad, FP64) against central finite differences of the
+CPU oracle, and the end-to-end gradient of a band-integrated spectral yield
+with respect to initial momenta and the laser a0 / waist (differentiable
+Boris pusher + LWSpectrum) against finite differences of the oracle fed by
+the workload generator's pusher.  Tolerance 1e-3 relative.
+
+The loss is continuous but its slope jumps whenever a sample's advanced time
+crosses a grid point; with central steps of 1e-6 (relative) such crossings
+move the difference quotient by up to ~1e-3, while at 1e-7 it has converged
+(checked at 1e-5 ... 1e-7), so the end-to-end check uses 1e-7."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2206_03015_gb300 import lw
+from paper_2206_03015_gb300.autograd import LWSpectrum, band_energy, band_mask, boris_push
+from workloads import simple
+from workloads.boris import GaussianLaser, boris_trajectories
+from workloads.planewave import doppler_fundamental
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+def _dirs(n, seed, max_angle):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tx = rng.uniform(-max_angle, max_angle, n)
+    ty = rng.uniform(-max_angle, max_angle, n)
+    return np.stack([np.sin(tx), np.cos(tx) * np.sin(ty), np.cos(tx) * np.cos(ty)], -1)
+
+
+def _oracle_loss(tr, n_hat, grid, w):
+    rec, _ = oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, n_hat, grid.t_min, grid.dt_u,
+                                grid.n_bins)
+    return float(np.sum(w * oracle.spectrum(rec, grid.dt_u)))
+
+
+def test_spectrum_grad_matches_oracle_finite_differences():
+    tr = simple.random_smooth(3, 60, 2e-18, 301, gamma=5.0, amp=0.5)
+    n_hat = _dirs(6, 7, 0.3)
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+    grid = lw.Grid(lo - 3 * (hi - lo) / 256, (hi - lo) / 250, 256)
+    rng = np.random.Generator(np.random.PCG64(9))
+    w = rng.uniform(0.5, 1.5, size=(6, 129))
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot, sections=lw.LW_SECTION_FP64)
+    det = lw.Detector(n_hat)
+    rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
+    S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, want_X=True)
+    g = lw.lw_spectrum_grad(traj, det, grid, X, torch.from_numpy(w).cuda())
+    grads = [x.cpu().numpy() for x in g]
+    torch.cuda.synchronize()
+    names = ("r", "beta", "beta_dot")
+    checked = 0
+    for which, arr in enumerate((tr.r, tr.beta, tr.beta_dot)):
+        scale = np.abs(arr).max()
+        for (k, i, c) in ((0, 17, 0), (1, 30, 2), (2, 44, 1), (0, 52, 2)):
+            h = 1e-6 * scale
+            plus = [a.copy() for a in (tr.r, tr.beta, tr.beta_dot)]
+            minus = [a.copy() for a in (tr.r, tr.beta, tr.beta_dot)]
+            plus[which][k, i, c] += h
+            minus[which][k, i, c] -= h
+            Lp = _oracle_loss(simple.Trajectories(tr.t, *plus), n_hat, grid, w)
+            Lm = _oracle_loss(simple.Trajectories(tr.t, *minus), n_hat, grid, w)
+            fd = (Lp - Lm) / (2 * h)
+            ref = max(abs(fd), 1e-3 * np.abs(grads[which]).max())
+            assert abs(grads[which][k, i, c] - fd) <= TOL * ref, (names[which], k, i, c,
+                                                                  grads[which][k, i, c], fd)
+            checked += 1
+    assert checked == 12
+
+
+def _c4_small():
+    laser = GaussianLaser(lam=1e-6, a0=1.0, w0=20e-6, fwhm=10e-15)
+    n_e, gamma = 6, 60.0
+    rng = np.random.Generator(np.random.PCG64(20603019))
+    g = gamma * (1.0 + 1e-3 * rng.normal(size=n_e))
+    uz = np.sqrt(g * g - 1.0)
+    u0 = np.stack([np.zeros(n_e), np.zeros(n_e), uz], -1)
+    sigma = laser.fwhm / (2.0 * math.sqrt(math.log(2.0)))
+    t_half = 0.5 * sigma * math.sqrt(2.0 * math.log(1e6))
+    # transverse offsets inside the waist so that w0 matters
+    r0 = np.stack([rng.uniform(-8e-6, 8e-6, n_e), rng.uniform(-8e-6, 8e-6, n_e),
+                   np.zeros(n_e)], -1) + (uz / g)[:, None] * np.array([0, 0, 299792458.0]) * -t_half
+    return laser, r0, u0, -t_half, t_half, 800, gamma
+
+
+def test_band_energy_gradient_wrt_initial_conditions_and_laser():
+    laser, r0, u0, t0, t1, n_s, gamma = _c4_small()
+    n_hat = _dirs(9, 11, 0.1 / gamma)
+    tr0 = boris_trajectories(r0, u0, laser, t0, t1, n_s)
+    lo, hi = oracle.grid_bounds(tr0.t, tr0.r, n_hat)
+    grid = lw.Grid(lo, (hi - lo) / 2048, 8192)          # 4x zero padding
+    w1 = doppler_fundamental(gamma, laser.lam, laser.a0)
+    mask = band_mask(grid, w1, 0.05).numpy()
+    assert mask.sum() >= 8
+    d_omega = 2 * math.pi / (grid.n_bins * grid.dt_u)
+    det = lw.Detector(n_hat)
+    dev = torch.device("cuda")
+    u = torch.tensor(u0, device=dev, requires_grad=True)
+    a0 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
+    w0 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
+    t, r, b, a = boris_push(torch.tensor(r0, device=dev), u, a0, w0, laser.lam, laser.fwhm, t0,
+                            t1, n_s, checkpoint_every=256)
+    S = LWSpectrum.apply(t, r, b, a, det, grid)
+    L = band_energy(S, grid, torch.from_numpy(mask))
+    L.backward()
+    torch.cuda.synchronize()
+
+    def L_oracle(u0_, a0_, w0_):
+        lz = GaussianLaser(lam=laser.lam, a0=a0_, w0=w0_, fwhm=laser.fwhm)
+        tr = boris_trajectories(r0, u0_, lz, t0, t1, n_s)
+        return _oracle_loss(tr, n_hat, grid, mask[None, :] * d_omega)
+
+    base = L_oracle(u0, laser.a0, laser.w0)
+    assert abs(float(L) / base - 1.0) < 1e-6     # torch and numpy pushers agree
+    checks = []
+    rel = 1e-7
+    for (k, c) in ((0, 2), (3, 0), (5, 2)):
+        h = rel * gamma
+        up, um = u0.copy(), u0.copy()
+        up[k, c] += h
+        um[k, c] -= h
+        checks.append((f"u0[{k},{c}]", float(u.grad[k, c]),
+                       (L_oracle(up, laser.a0, laser.w0) - L_oracle(um, laser.a0, laser.w0)) / (2 * h)))
+    h = rel * laser.a0
+    checks.append(("a0", float(a0.grad),
+                   (L_oracle(u0, laser.a0 + h, laser.w0) - L_oracle(u0, laser.a0 - h, laser.w0)) / (2 * h)))
+    h = rel * laser.w0
+    checks.append(("w0", float(w0.grad),
+                   (L_oracle(u0, laser.a0, laser.w0 + h) - L_oracle(u0, laser.a0, laser.w0 - h)) / (2 * h)))
+    for name, g, fd in checks:
+        assert abs(g - fd) <= TOL * abs(fd), (name, g, fd)

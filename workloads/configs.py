@@ -104,3 +104,49 @@ def c4_grad(n_e=2048, n_s=4096, nx=32, n_bins=16_384) -> Workload:
     laser = GaussianLaser(lam=1e-6, a0=1.0, w0=20e-6, fwhm=10e-15)
     return _c2_like("c4_grad", n_e, n_s, nx, n_bins, 0.0, 0.0, 0.0, SEED_BASE + 4,
                     half_angle_g=1.0, laser=laser, eps_n=0.0)
+
+
+def c5_batch(n_variants=64, seed=SEED_BASE + 5, n_e=(512, 8192), n_s=(2000, 40000),
+             nx=(16, 128), log2_bins=(12, 17), gamma=(20.0, 200.0), a0=(0.05, 1.0)):
+    """Batched design sweep: independent variants with gamma log-uniform, a0 uniform,
+    electrons / steps / detector side log-uniform and 2^U{log2_bins} observer bins;
+    each variant is a Gaussian bunch (as c2_paper) in a 0.8 um Gaussian laser.
+    The default ranges are the full sweep; tests and benches pass smaller ranges.
+    Returns a list of Workloads (trajectories generated lazily by ``.build()``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def logu(lo, hi, size):
+        return np.exp(rng.uniform(np.log(lo), np.log(hi), size))
+
+    g = logu(gamma[0], gamma[1], n_variants)
+    a = rng.uniform(a0[0], a0[1], n_variants)
+    ne = np.round(logu(n_e[0], n_e[1], n_variants)).astype(int)
+    ns = np.round(logu(n_s[0], n_s[1], n_variants)).astype(int)
+    side = np.round(logu(nx[0], nx[1], n_variants)).astype(int)
+    lb = rng.integers(log2_bins[0], log2_bins[1] + 1, n_variants)
+    out = []
+    for v in range(n_variants):
+        laser = GaussianLaser(lam=0.8e-6, a0=float(a[v]), w0=20e-6, fwhm=30e-15)
+        out.append(_LazyVariant(f"c5_v{v}", int(ne[v]), int(ns[v]), int(side[v]), 1 << int(lb[v]),
+                                float(g[v]), laser, seed + 1000 + v))
+    return out
+
+
+@dataclass
+class _LazyVariant:
+    name: str
+    n_e: int
+    n_s: int
+    nx: int
+    n_bins: int
+    gamma: float
+    laser: GaussianLaser
+    seed: int
+
+    @property
+    def deposits(self):
+        return self.n_e * self.n_s * self.nx * self.nx
+
+    def build(self) -> Workload:
+        return _c2_like(self.name, self.n_e, self.n_s, self.nx, self.n_bins, 5e-6, 5e-6, 10e-6,
+                        self.seed, laser=self.laser, gamma=self.gamma)
