@@ -262,16 +262,20 @@ typedef struct {
 /* Trajectory update of Algorithm 2 ("update trajectory", Boris method as in the
  * paper's trial simulation) for the in-situ form of the path: advances n_e
  * particles (r [n_e][3] in metres, u = gamma beta [n_e][3]; device, updated in
- * place) by n_steps steps of dt from time t0 in the Gaussian laser, and writes
- * the n_steps + 1 samples t_out [n_steps+1], r_out, beta_out, bdot_out
+ * place) by n_steps steps of dt from time t0 + step0 dt in the Gaussian laser,
+ * and writes the n_steps + 1 samples t_out [n_steps+1], r_out, beta_out, bdot_out
  * [n_e][n_steps+1][3] (device, FP64) -- the layout of lw_traj_in -- including the
  * starting state as sample 0, so consecutive calls overlap by one sample.
+ * Sample s has the time t0 + dt (step0 + s) (FP64, that order of operations), so
+ * pushing in blocks with a running step0 and one t0 gives bit-identical times and
+ * trajectories to a single call.  step0 in [0, 2^52].
  * Step: drift dt/2, Boris kick with the fields at the midpoint, drift dt/2;
  * bdot = q/(m gamma c0) [E + c0 beta x B - beta (beta.E)] at each sample.
  * Errors: LW_EINVAL, LW_ECUDA. */
-int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int32_t n_steps,
-                  const lw_laser* laser, double charge, double mass, double* t_out,
-                  double* r_out, double* beta_out, double* bdot_out, void* stream);
+int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64_t step0,
+                  int32_t n_steps, const lw_laser* laser, double charge, double mass,
+                  double* t_out, double* r_out, double* beta_out, double* bdot_out,
+                  void* stream);
 
 /* Several independent problems ("variants": own trajectories, detector, grid
  * and record) deposited by one persistent launch of the mixed-precision

@@ -62,7 +62,7 @@ __device__ __forceinline__ void store_sample(const Laser& L, double qm, const do
 }
 
 __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int64_t n_e,
-                            double t0, double dt, int n_steps, Laser L, double qm,
+                            double t0, double dt, int64_t step0, int n_steps, Laser L, double qm,
                             double* __restrict__ ro, double* __restrict__ bo,
                             double* __restrict__ ao) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
@@ -70,10 +70,11 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
         double x[3] = {r[3 * k], r[3 * k + 1], r[3 * k + 2]};
         double v[3] = {u[3 * k], u[3 * k + 1], u[3 * k + 2]};
         const int64_t base = k * (int64_t)(n_steps + 1);
-        store_sample(L, qm, x, v, t0, ro + 3 * base, bo + 3 * base, ao + 3 * base);
+        store_sample(L, qm, x, v, t0 + dt * (double)step0, ro + 3 * base, bo + 3 * base,
+                     ao + 3 * base);
         const double eps = qm * dt / (2.0 * kC0);
         for (int s = 0; s < n_steps; ++s) {
-            const double ti = t0 + dt * s;
+            const double ti = t0 + dt * (double)(step0 + s);
             double gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
             const double rh[3] = {x[0] + 0.5 * dt * kC0 * v[0] / gam,
                                   x[1] + 0.5 * dt * kC0 * v[1] / gam,
@@ -94,7 +95,7 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
             x[1] = rh[1] + 0.5 * dt * kC0 * v[1] / gam;
             x[2] = rh[2] + 0.5 * dt * kC0 * v[2] / gam;
             const int64_t o = 3 * (base + s + 1);
-            store_sample(L, qm, x, v, t0 + dt * (s + 1), ro + o, bo + o, ao + o);
+            store_sample(L, qm, x, v, t0 + dt * (double)(step0 + s + 1), ro + o, bo + o, ao + o);
         }
         r[3 * k] = x[0];
         r[3 * k + 1] = x[1];
@@ -105,9 +106,9 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
     }
 }
 
-__global__ void times_kernel(double* t_out, double t0, double dt, int n_steps) {
+__global__ void times_kernel(double* t_out, double t0, double dt, int64_t step0, int n_steps) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= n_steps; s += gridDim.x * blockDim.x)
-        t_out[s] = t0 + dt * s;
+        t_out[s] = t0 + dt * (double)(step0 + s);
 }
 
 }  // namespace
@@ -116,11 +117,14 @@ __global__ void times_kernel(double* t_out, double t0, double dt, int n_steps) {
 using namespace lw;
 
 extern "C" int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt,
-                             int32_t n_steps, const lw_laser* laser, double charge, double mass,
+                             int64_t step0, int32_t n_steps, const lw_laser* laser,
+                             double charge, double mass,
                              double* t_out, double* r_out, double* beta_out, double* bdot_out,
                              void* stream) {
     if (!r || !u || !laser || !t_out || !r_out || !beta_out || !bdot_out) return LW_EINVAL;
-    if (n_e < 1 || n_steps < 1 || !(dt > 0.0) || !isfinite(t0) || !(mass > 0.0)) return LW_EINVAL;
+    if (n_e < 1 || n_steps < 1 || step0 < 0 || step0 > (int64_t(1) << 52) || !(dt > 0.0) ||
+        !isfinite(t0) || !(mass > 0.0))
+        return LW_EINVAL;
     if (!(laser->lam > 0.0) || !(laser->w0 > 0.0) || !(laser->fwhm > 0.0)) return LW_EINVAL;
     Laser L;
     L.omega = 2.0 * kPi * kC0 / laser->lam;
@@ -130,11 +134,11 @@ extern "C" int lw_boris_push(double* r, double* u, int64_t n_e, double t0, doubl
     L.zR = kPi * laser->w0 * laser->w0 / laser->lam;
     L.w0 = laser->w0;
     cudaStream_t st = as_stream(stream);
-    times_kernel<<<(n_steps + 256) / 256, 256, 0, st>>>(t_out, t0, dt, n_steps);
+    times_kernel<<<(n_steps + 256) / 256, 256, 0, st>>>(t_out, t0, dt, step0, n_steps);
     if (launch_status() != LW_OK) return LW_ECUDA;
     const int threads = 128;
     const int blocks = (int)((n_e + threads - 1) / threads);
-    push_kernel<<<blocks, threads, 0, st>>>(r, u, n_e, t0, dt, n_steps, L, charge / mass, r_out,
+    push_kernel<<<blocks, threads, 0, st>>>(r, u, n_e, t0, dt, step0, n_steps, L, charge / mass, r_out,
                                             beta_out, bdot_out);
     return launch_status();
 }

@@ -48,7 +48,7 @@ def in_situ_spectrum(r0, u0, laser, t_start: float, t_end: float, n_steps: int,
         r, u = r0.clone(), u0.clone()
         for s0 in range(0, n_steps, B):
             nb = min(B, n_steps - s0)
-            lw.lw_boris_push(r, u, t_start + s0 * dt, dt, nb, laser, t_b, *bufs)
+            lw.lw_boris_push(r, u, t_start, dt, nb, laser, t_b, *bufs, step0=s0)
         lo, hi = grid_bounds_from_ends(t_start, t_start + n_steps * dt, r0, r, det)
         grid = lw.grid_from_bounds(lo, hi, n_bins)
     shp, dtype = lw.record_shape(det, grid, precision)
@@ -58,7 +58,7 @@ def in_situ_spectrum(r0, u0, laser, t_start: float, t_end: float, n_steps: int,
     ws = None
     for s0 in range(0, n_steps, B):
         nb = min(B, n_steps - s0)
-        lw.lw_boris_push(r, u, t_start + s0 * dt, dt, nb, laser, t_b, *bufs)
+        lw.lw_boris_push(r, u, t_start, dt, nb, laser, t_b, *bufs, step0=s0)
         views = [x[: n_e * (nb + 1) * 3].view(n_e, nb + 1, 3) for x in bufs]
         traj = lw.lw_trajectories_upload(t_b[: nb + 1], *views, sections=sections,
                                          block=anchor_block, device=dev, ws=ws)

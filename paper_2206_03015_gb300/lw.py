@@ -118,8 +118,8 @@ def load(build_if_missing: bool = True):
                                          P, P, ctypes.c_double, P, P, P, P,
                                          ctypes.POINTER(ctypes.c_size_t), P]
         lib.lw_boris_push.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_int32, ctypes.POINTER(lw_laser), ctypes.c_double,
-                                      ctypes.c_double, P, P, P, P, P]
+                                      ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(lw_laser),
+                                      ctypes.c_double, ctypes.c_double, P, P, P, P, P]
         lib.lw_spectrum_fdm.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector),
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         ctypes.c_double, ctypes.c_double, P, P]
@@ -421,14 +421,16 @@ M_E = 9.1093837015e-31
 
 
 def lw_boris_push(r, u, t0: float, dt: float, n_steps: int, laser, t_out, r_out, beta_out,
-                  bdot_out, charge: float = -Q_E, mass: float = M_E):
+                  bdot_out, charge: float = -Q_E, mass: float = M_E, step0: int = 0):
     """Advance (r, u) [n_e, 3] (float64 CUDA tensors, in place) by n_steps Boris steps in the
     Gaussian laser (lam, a0, w0, fwhm) and write the n_steps+1 samples into the outputs
-    (t_out [n_steps+1], r_out/beta_out/bdot_out [n_e, n_steps+1, 3])."""
+    (t_out [n_steps+1], r_out/beta_out/bdot_out [n_e, n_steps+1, 3]); sample s is at time
+    t0 + dt (step0 + s)."""
     lib = load()
     L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
     _check("lw_boris_push", lib.lw_boris_push(_ptr(r), _ptr(u), r.shape[0], float(t0),
-                                              float(dt), int(n_steps), ctypes.byref(L),
+                                              float(dt), int(step0), int(n_steps),
+                                              ctypes.byref(L),
                                               float(charge), float(mass), _ptr(t_out),
                                               _ptr(r_out), _ptr(beta_out), _ptr(bdot_out),
                                               _stream()))

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def variants():
-    vs = configs.c5_batch(n_variants=6, n_e=(12, 48), n_s=(300, 1200), nx=(4, 12),
+    vs = configs.c5_batch(n_variants=6, n_e=(12, 48), n_s=(2500, 5000), nx=(4, 12),
                           log2_bins=(10, 13))
     out = []
     for v in vs:
