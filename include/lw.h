@@ -313,6 +313,27 @@ int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_t precision
                   void* stream);
 int lw_batch_deposit(const lw_batch* plan, void* stream);
 
+/* lw_spectrum without a caller-supplied workspace, for callers that must not
+ * allocate device memory while they run -- for example a read-out or plug-in
+ * process whose device memory budget is fixed at start-up, where a cudaMalloc
+ * or cudaFree would also synchronise the whole device and stall unrelated
+ * streams.  The paper has no counterpart; this is a deployment convenience.
+ * Same arguments, results and errors as lw_spectrum, except that the scratch
+ * is one fixed array of lw_spectrum_static_capacity() bytes (32 MiB) that
+ * every GPU loading the library holds until the process exits:
+ *  - transforms whose scratch would exceed it return LW_ESIZE (n_bins <= 4096
+ *    needs only the twiddle table; above that the four-step buffer needs
+ *    3 * ceil(n_pix/2) * n_bins complex values);
+ *  - the first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture;
+ *  - all calls share the array and nothing in it needs to start at zero, but
+ *    calls that overlap on the GPU (other streams, other host threads) race
+ *    on it: serialise them.
+ * No device or host allocation is made by this call. */
+int lw_spectrum_static(const void* record, int32_t precision, int64_t n_pix, const lw_grid* grid,
+                       double q, void* spectrum, void* X_save, void* stream);
+size_t lw_spectrum_static_capacity(void);
+
 #ifdef __cplusplus
 }
 #endif

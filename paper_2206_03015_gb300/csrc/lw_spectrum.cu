@@ -17,6 +17,8 @@
 //               the split above.
 #include <math.h>
 
+#include <mutex>
+
 #include "lw_fft.cuh"
 
 namespace lw {
@@ -293,3 +295,59 @@ extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
                                X_save, ws, ws_bytes, st);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of lw_spectrum.  Its scratch (twiddle table and, for
+// n_bins above 4096, the four-step transform buffer) lives in one fixed
+// device array owned by this library instead of a caller-supplied workspace.
+namespace lw {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB per GPU
+__device__ __align__(256) unsigned char g_spectrum_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_spectrum_scratch on the current device, looked up once
+// per device (in host code the array's name is not a device address).
+int static_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LW_ECUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_spectrum_scratch) != cudaSuccess || !ptr)
+            return LW_ECUDA;
+        g_scratch_ptr[dev] = ptr;
+    }
+    *out = g_scratch_ptr[dev];
+    return LW_OK;
+}
+
+}  // namespace
+}  // namespace lw
+
+extern "C" size_t lw_spectrum_static_capacity(void) { return lw::kStaticScratchBytes; }
+
+extern "C" int lw_spectrum_static(const void* record, int32_t precision, int64_t n_pix,
+                                  const lw_grid* grid, double q, void* spectrum, void* X_save,
+                                  void* stream) {
+    if (!grid || n_pix < 1 || !record || !spectrum) return LW_EINVAL;
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+        return LW_EINVAL;
+    const int64_t N = grid->n_bins;
+    if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;
+    if (!(grid->dt_u > 0.0) || !isfinite(q)) return LW_EINVAL;
+    size_t need = 0;
+    int rc = lw_spectrum(record, precision, n_pix, grid, q, spectrum, X_save, nullptr, &need,
+                         stream);
+    if (rc != LW_OK) return rc;
+    if (need > lw::kStaticScratchBytes) return LW_ESIZE;
+    void* scratch = nullptr;
+    rc = lw::static_scratch(&scratch);
+    if (rc != LW_OK) return rc;
+    size_t bytes = lw::kStaticScratchBytes;
+    return lw_spectrum(record, precision, n_pix, grid, q, spectrum, X_save, scratch, &bytes,
+                       stream);
+}

@@ -83,7 +83,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain", "lw_spectrum",
-           "lw_spectrum_grad", "lw_batch_plan", "lw_batch_deposit",
+           "lw_spectrum_grad", "lw_spectrum_static", "lw_batch_plan", "lw_batch_deposit",
            "lw_spectrum_fdm", "lw_boris_push")
 
 
@@ -128,6 +128,10 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(lw_batch),
                                       P]
         lib.lw_batch_deposit.argtypes = [ctypes.POINTER(lw_batch), P]
+        lib.lw_spectrum_static.argtypes = [P, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.POINTER(lw_grid), ctypes.c_double, P, P, P]
+        lib.lw_spectrum_static_capacity.argtypes = []
+        lib.lw_spectrum_static_capacity.restype = ctypes.c_size_t
         for f in EXPORTS:
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -434,3 +438,28 @@ def lw_boris_push(r, u, t0: float, dt: float, n_steps: int, laser, t_out, r_out,
                                               float(charge), float(mass), _ptr(t_out),
                                               _ptr(r_out), _ptr(beta_out), _ptr(bdot_out),
                                               _stream()))
+
+
+def lw_spectrum_static(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E,
+                       want_X=False, out=None):
+    """lw_spectrum without a workspace argument: the library's fixed device scratch
+    array is used instead (see include/lw.h); nothing is allocated by the library.
+    Output tensors are allocated here unless passed in."""
+    lib = load()
+    dev = record.device
+    dtype = torch.float64 if precision == LW_FP64 else torch.float32
+    nl = grid.n_bins // 2 + 1
+    S = out if out is not None else torch.empty((n_pix, nl), dtype=dtype, device=dev)
+    X = torch.empty((n_pix, 3, nl, 2), dtype=dtype, device=dev) if want_X else None
+    g = grid.c()
+    rc = lib.lw_spectrum_static(_ptr(record), precision, n_pix, ctypes.byref(g), q, _ptr(S),
+                                _ptr(X), _stream())
+    if rc == LW_ESIZE:
+        cap = lib.lw_spectrum_static_capacity()
+        raise LWError("lw_spectrum_static", rc) from ValueError(
+            f"this transform needs more scratch than the fixed {cap} bytes; use lw_spectrum")
+    _check("lw_spectrum_static", rc)
+    if want_X:
+        return S, torch.view_as_complex(X)
+    return S
+
