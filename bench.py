@@ -120,6 +120,26 @@ def _traffic_from_profile(kernel_src):
     return d.get("bytes_per_launch_full_size")
 
 
+def grid_points_reached(t, r, det, grid, chunk=256):
+    """Grid points deposited by the whole workload: per (pixel, electron), the points of
+    (floor(u_first), floor(u_last)] inside [0, n_bins), u = (t_a - t_min)/dt_u of the
+    trajectory's first and last sample (FP64, torch on the device; bookkeeping only)."""
+    import torch
+    c0 = 299792458.0
+    t0 = t[0] if t.dim() == 1 else t[:, 0]
+    t1 = t[-1] if t.dim() == 1 else t[:, -1]
+    r0, r1 = r[:, 0, :], r[:, -1, :]
+    total = 0
+    for m0 in range(0, det.n_pix, chunk):
+        n = det.n_hat[m0:m0 + chunk]
+        u0 = ((t0 - (r0 @ n.T).T / c0) - grid.t_min) / grid.dt_u
+        u1 = ((t1 - (r1 @ n.T).T / c0) - grid.t_min) / grid.dt_u
+        j0 = torch.clamp(torch.floor(u0) + 1, min=0)
+        j1 = torch.clamp(torch.floor(u1), max=grid.n_bins - 1)
+        total += int(torch.clamp(j1 - j0 + 1, min=0).sum().item())
+    return total
+
+
 # ----------------------------------------------------------------------------- workload
 
 def make_workload(args, rank):
@@ -226,23 +246,33 @@ def run_ours(args, rank, world, dist):
                    "parallelism": f"detector-sharded x{world} (one detector per GPU)",
                    "generation_s": round(t_gen, 1)},
     }
-    # roofline of the dominant kernel (mixed deposit): ALU bound, FP32 lanes
-    alg_flops_per_dep = 9.0     # 4 FFMA (8 flops) + 1 compare per electron-step-pixel
-    sm_max = 2070.0
+    # roofline of the dominant kernel (mixed deposit) against HBM: the algorithmic bytes
+    # of one launch are its inputs read once (mixed trajectory section: float4 scan +
+    # six field floats per sample, one FP64 anchor per block) and the record written
+    # once; its updates are 3 atomics per grid point reached (counted from the exact
+    # bins of each (pixel, electron) trajectory's first and last sample)
+    hbm_peak, peak_src = 6800.0, "fallback"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
-    except (OSError, ValueError):
+            hbm_peak, peak_src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
         pass
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FP32 FMA lanes at max clock
-    achieved = alg_flops_per_dep * n_dep / (dep_ms * 1e-3) / 1e12
+    ns1 = tr.n_s + 1
+    n_blocks = -(-ns1 // args.block)
+    traj_bytes = tr.n_e * (ns1 * (16 + 24) + n_blocks * 32)
+    rec_bytes = w.n_pix * 3 * w.n_bins * 8
+    alg_bytes = traj_bytes + rec_bytes
+    achieved = alg_bytes / (dep_ms * 1e-3) / 1e9
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2206_03015_gb300", "csrc",
                                                  "lw_deposit.cu"))
-    result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
-                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+    n_points = grid_points_reached(t_d, r_d, det, grid)
+    result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                          "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                           "kernel": "deposit_mixed_kernel", "kernel_ms": dep_ms,
-                          "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz "
-                                       "(derived, not measured)" % sm_max}
+                          "algorithmic_bytes": alg_bytes,
+                          "grid_points": n_points,
+                          "atomics_per_s": 3.0 * n_points / (dep_ms * 1e-3)}
     result["clocks"] = clocks
     torch.cuda.synchronize()
     st_m = int(status.item())

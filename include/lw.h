@@ -121,6 +121,10 @@ typedef struct {
     const double* ends;     /* always: double [n_e][2][4] = (t, x, y, z) of the first and
                                the last sample of each electron */
     const int32_t* input_status; /* device int32: LW_ST_* found while uploading */
+    const int32_t* order;   /* MIXED: int32 [n_e] electron indices in increasing light-front
+                               time tau = t - z/c0 of the first sample (bucketed: the order
+                               within 1/4096 of the range is unspecified); the mixed
+                               deposit visits electrons in this order */
 } lw_traj;
 
 /* Far-field detector: n_pix unit directions n_hat [n_pix][3] (float64, device) on a
@@ -148,8 +152,13 @@ typedef struct {
  *   out        filled with the device view on success
  * Checks every sample (finite values, |beta| < 1, strictly increasing t) and
  * records LW_ST_* bits in the workspace for later deposits.
+ * The mixed deposit relies on the advanced time increasing along each
+ * trajectory for every direction, which holds whenever consecutive samples
+ * are less than c0 (t_i - t_{i-1}) apart, i.e. for any subluminal motion
+ * sampled in time order; the FP64 deposit makes no such assumption.
  * Errors: LW_EINVAL (null in/out pointers, n_e < 1, n_s < 1, bad sections or
- * block), LW_ESIZE (ws too small; *ws_bytes = required), LW_ECUDA. */
+ * block), LW_EUNSUPPORTED (n_s >= 2^30 or n_e >= 2^31), LW_ESIZE (ws too small; *ws_bytes =
+ * required), LW_ECUDA. */
 int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, int32_t block, void* ws,
                            size_t* ws_bytes, lw_traj* out, void* stream);
 

@@ -4,24 +4,28 @@
 // pixel(s) -- the paper's "detector parallelization" on one GPU -- and a CTA
 // walks a chunk of electrons; the samples of the current electron are staged
 // in shared memory once per CTA and read by all of its pixels as broadcasts.
-// Each step costs the time map and one compare; the field (Eq. far_efield)
-// and the interpolation weights are evaluated only when the step's interval
-// (t_b, t_a] contains grid points, and those contributions are added to the
-// record with global atomics (pixels of different CTAs share bins through
-// electrons of other chunks).
+// The field (Eq. far_efield) and the interpolation weights are evaluated only
+// for steps whose interval (t_b, t_a] contains grid points, and those
+// contributions are added to the record with global atomics (pixels of
+// different CTAs share bins through electrons of other chunks).
 //
-// FP64 path: every operation of the time map, the bin index, the field and
-// the weights is written with explicit round-to-nearest intrinsics in the
-// order documented in lw.h, so advanced times, bin indices and per-sample
-// contributions are bit-identical to a plain C loop without FMA contraction;
-// only the order of the atomic additions differs.
+// FP64 path: every step costs the time map and one compare.  Every operation
+// of the time map, the bin index, the field and the weights is written with
+// explicit round-to-nearest intrinsics in the order documented in lw.h, so
+// advanced times, bin indices and per-sample contributions are bit-identical
+// to a plain C loop without FMA contraction; only the order of the atomic
+// additions differs.
 //
 // Mixed path: the bin coordinate u = (t_a - t_min)/dt_u is anchored once per
 // block of samples in double-FP32 arithmetic (integer part + FP32 fraction)
-// and advanced per sample with four FP32 FMAs of small, block-relative
-// quantities; the field is FP32 in the stable form
+// and evaluated per sample with three FP32 FMAs of small, block-relative
+// quantities.  Because t_a increases along a subluminal trajectory, a block
+// needs one coordinate per pixel (its last sample) to know which grid points
+// it reaches; each grid point's step is then found by bisection over the
+// staged block.  The field is FP32 in the stable form
 //   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
-// and contributions are added with a compensated pair of FP32 atomics.
+// and contributions are added with FP64 atomics (or a compensated pair of
+// FP32 atomics).
 #include <math.h>
 
 #include <algorithm>
@@ -45,6 +49,7 @@ struct DepositArgs {
     int block, n_blocks;
     const int32_t* input_status;
     const double* ends;
+    const int32_t* order;   // mixed: electron visiting order (may be null)
     const double* n_hat;
     int64_t n_pix;
     double R;
@@ -249,18 +254,9 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __
     }
 }
 
-// A step whose interval (t_b, t_a] contains grid points, recorded by the scan
-// loop of one lane and deposited later by the whole warp (16 bytes).
-struct Event {
-    unsigned packed;   // slot (lane * PIX + q, 7 bits) | qq << 7 (10 bits) | cnt << 17 (15 bits)
-    int ja;            // first grid point (clipped)
-    float a0;          // ja - u_{i-1}   [bins]
-    float du;          // u_i - u_{i-1}  [bins]
-};
-constexpr int kMaxEventBins = (1 << 15) - 1;
-
-constexpr int kLaneQ = 8;                       // events per lane between drains
-constexpr int kWarps = kMixThreads / 32;
+// Grid points of one pixel and block above which the owning lane deposits them
+// itself instead of handing them to the warp (keeps the warp's job count in int).
+constexpr int kMaxWarpJobs = 1 << 20;
 
 template <bool KAHAN>
 __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
@@ -283,32 +279,58 @@ __device__ __forceinline__ int exact_bin(const double* e, double nx, double ny, 
 // Bin coordinate of a staged sample relative to the block anchor, without the
 // anchor fraction f: sc.x holds C = s*dtau + w_c . dr for the CTA's reference
 // slope w_c, dw = w_pixel - w_c, so u - I - f = C + dw . dr.
-template <int PIX>
-__device__ __forceinline__ float coord(const float (&dw)[PIX][3], int q, float4 sc) {
-    return fmaf(dw[q][2], sc.w, fmaf(dw[q][1], sc.z, fmaf(dw[q][0], sc.y, sc.x)));
+__device__ __forceinline__ float coord(float4 dw, float4 sc) {
+    return fmaf(dw.z, sc.w, fmaf(dw.y, sc.z, fmaf(dw.x, sc.y, sc.x)));
+}
+
+// Grid point J (relative to the anchor integer) is reached by a sample of
+// coordinate x when fl(J - f) <= x.  Returns the largest such J, by the same
+// FP32 comparison the crossing search makes, so the two always agree.
+__device__ __forceinline__ int last_point(float x, float f) {
+    const float s = fminf(fmaxf(__fadd_rn(x, f), -1.0e9f), 1.0e9f);
+    int J = (int)floorf(s);
+    if (__fsub_rn((float)(J + 1), f) <= x)
+        ++J;
+    else if (__fsub_rn((float)J, f) > x)
+        --J;
+    return J;
 }
 
 // The work of one CTA: pixel tile `tile` (kMixThreads * PIX pixels) and electron
 // chunk `chunk` (p.e_chunk electrons) of one variant.  Returns the status bits.
+//
+// The advanced time of a subluminal particle increases strictly along its
+// trajectory (dt_a/dt = 1 - n.beta > 0), so per pixel the grid points that a
+// block of samples reaches form one run (j_done, j_end], where j_end follows
+// from the block's last sample alone, and each of them lies in exactly one
+// step (t_{i-1}, t_i] of Algorithm 2: the first sample i whose coordinate
+// reaches it, found by bisection over the staged block.  Per block a lane
+// evaluates one coordinate per pixel; the grid points of the warp's 128
+// pixels are then spread over its 32 lanes (prefix sum of the runs, one grid
+// point per lane and round), each lane finding its step, evaluating the two
+// fields and adding the interpolated value.
 template <int PIX, bool KAHAN>
 __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     extern __shared__ float4 smem4[];
+    constexpr int kSlots = kMixThreads * PIX;
     const int B = p.block;
     float4* s_scan = smem4;                                    // [B] (C, dx, dy, dz)
     float* s_field = reinterpret_cast<float*>(smem4 + B);      // [B+1][6], sample i0-1 first
     __shared__ float s_anch[8];                                // T, R_x, R_y, R_z (hi, lo)
     __shared__ float s_wc[3];                                  // reference slope of the CTA
-    __shared__ Event s_q[kWarps][kLaneQ * 32];                 // [warp][lane * kLaneQ + e]
-    __shared__ int s_qn[kWarps][32];
-    __shared__ float s_w[kMixThreads * PIX][6];                // slopes: hi parts, lo parts
-    __shared__ int s_jlast[kMixThreads * PIX];                 // exact bin of the last sample
+    __shared__ float s_w[kSlots][6];                           // slopes: hi parts, lo parts
+    __shared__ float4 s_dw[kSlots];                            // slope - reference slope
+    __shared__ float4 s_pc[kSlots];                            // n_x, n_y, n_z, 1 - n_z (FP32)
+    __shared__ int4 s_job[kSlots];                             // block: I, first point, f, v_prev
+    __shared__ int s_kp[kSlots];                               // block: job offset in the warp
+    __shared__ int s_jlast[kSlots];                            // exact bin of the last sample
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wslot = warp * 32 * PIX;
     const float s32 = (float)p.inv_dtu;
     const float c0_over_R = (float)(kC0 / p.R);
     const int nb = (int)p.n_bins;
-    const int64_t pix0 = tile * kMixThreads * PIX;
+    const int64_t pix0 = tile * kSlots;
     unsigned act = 0;
     __syncthreads();   // shared arrays may still be read by the previous unit
     for (int q = 0; q < PIX; ++q) {
@@ -324,13 +346,15 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
         const double sc = kInvC0 * p.inv_dtu;
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
-        float* w = s_w[wslot + lane * PIX + q];
+        const int sl = wslot + lane * PIX + q;
+        float* w = s_w[sl];
         w[0] = wx.hi;
         w[1] = wy.hi;
         w[2] = wz.hi;
         w[3] = wx.lo;
         w[4] = wy.lo;
         w[5] = wz.lo;
+        s_pc[sl] = make_float4((float)nx, (float)ny, (float)nz, (float)omnz);
         if (threadIdx.x == 0 && q == 0) {
             s_wc[0] = wx.hi;
             s_wc[1] = wy.hi;
@@ -338,77 +362,73 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
         }
     }
     __syncthreads();
-    float dw[PIX][3];
-    for (int q = 0; q < PIX; ++q)
-        for (int c = 0; c < 3; ++c) dw[q][c] = s_w[wslot + lane * PIX + q][c] - s_wc[c];
+    for (int q = 0; q < PIX; ++q) {
+        const int sl = wslot + lane * PIX + q;
+        s_dw[sl] = make_float4(s_w[sl][0] - s_wc[0], s_w[sl][1] - s_wc[1], s_w[sl][2] - s_wc[2],
+                               0.0f);
+    }
     const float wcx = s_wc[0], wcy = s_wc[1], wcz = s_wc[2];
-    Event* myq = s_q[warp] + lane * kLaneQ;
-    int* qn = s_qn[warp];
-    int nq = 0;                                  // this lane's queued events
     int bits = 0;
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
 
-    // pixel (global index) of warp slot `sl`
+    // pixel (global index) of slot `sl`
     auto slot_pixel = [&](int sl) -> int64_t {
-        const int ln = sl / PIX, q = sl % PIX;
-        return pix0 + q * kMixThreads + warp * 32 + ln;
+        const int w = sl / (32 * PIX), r = sl % (32 * PIX);
+        return pix0 + (r % PIX) * kMixThreads + w * 32 + r / PIX;
     };
-    // deposit the grid points [ja, ja+cnt) of one crossing of pixel `m`
-    auto deposit = [&](int64_t m, int qq, int ja, int cnt, float a0, float du) {
-        const double* nh = p.n_hat + 3 * m;
-        PixelConst pc;
-        pc.nx = (float)nh[0];
-        pc.ny = (float)nh[1];
-        pc.nz = (float)nh[2];
-        pc.omnz = (pc.nx * pc.nx + pc.ny * pc.ny) / (1.0f + pc.nz);   // no cancellation
-        const int64_t base = m * 3 * p.n_bins;
+    // deposit grid point j (absolute) of slot `sl` in the staged block of n samples;
+    // lo0 = first sample that may end a step (1 in the trajectory's first block)
+    auto job = [&](int sl, int j, int lo0, int n) {
+        const int4 jb = s_job[sl];
+        const float f = __int_as_float(jb.z);
+        const float4 dw = s_dw[sl];
+        const float J = (float)(j - jb.x);
+        const float tJ = __fsub_rn(J, f);
+        int lo = lo0, hi = n - 1;   // first sample reaching tJ; the last one if none does
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (coord(dw, s_scan[mid]) >= tJ)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const float vi = __fadd_rn(coord(dw, s_scan[lo]), f);
+        const float vp = lo > 0 ? __fadd_rn(coord(dw, s_scan[lo - 1]), f) : __int_as_float(jb.w);
+        const float a0 = __fsub_rn(J, vp);
+        const float du = __fsub_rn(vi, vp);
+        const float4 c = s_pc[sl];
+        const PixelConst pc{c.x, c.y, c.z, c.w};
         float Fb[3], Fa[3];
-        field_fp32(pc, s_field + 6 * qq, p.flags, c0_over_R, Fb);
-        field_fp32(pc, s_field + 6 * (qq + 1), p.flags, c0_over_R, Fa);
+        field_fp32(pc, s_field + 6 * lo, p.flags, c0_over_R, Fb);
+        field_fp32(pc, s_field + 6 * (lo + 1), p.flags, c0_over_R, Fa);
         const float inv_du = du > 0.0f ? 1.0f / du : 0.0f;
-        for (int t = 0; t < cnt; ++t) {
-            const float wb = (a0 + (float)t) * inv_du;
-            const float wa = 1.0f - wb;
-            const int64_t j = base + ja + t;
-            accumulate<KAHAN>(p.record, j, fmaf(Fb[0], wa, Fa[0] * wb));
-            accumulate<KAHAN>(p.record, j + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-            accumulate<KAHAN>(p.record, j + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
-        }
-    };
-    // deposit every queued event of the warp with all 32 lanes
-    auto drain = [&]() {
-        qn[lane] = nq;
-        __syncwarp();
-        for (int e = lane; e < 32 * kLaneQ; e += 32) {
-            const int owner = e / kLaneQ, idx = e % kLaneQ;
-            if (idx >= qn[owner]) continue;
-            const Event ev = s_q[warp][owner * kLaneQ + idx];
-            deposit(slot_pixel((int)(ev.packed & 127u)), (int)((ev.packed >> 7) & 1023u), ev.ja,
-                    (int)(ev.packed >> 17), ev.a0, ev.du);
-        }
-        __syncwarp();
-        nq = 0;
+        const float wb = a0 * inv_du;
+        const float wa = 1.0f - wb;
+        const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
+        accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
+        accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+        accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
     };
 
     const int64_t k0 = chunk * p.e_chunk;
     const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
-    for (int64_t k = k0; k < k1; ++k) {
+    for (int64_t kk = k0; kk < k1; ++kk) {
+        const int64_t k = p.order ? (int64_t)p.order[kk] : kk;
         const float4* sck = p.scan + k * p.ns1;
         const float* fdk = p.field + 6 * k * p.ns1;
         const D4* anc = p.anchor + k * p.n_blocks;
         const double* ends = p.ends + 8 * k;
-        // per pixel: I = integer anchor of the block, f = U_b - I, thr = next grid point
-        // relative to I (floor(u_{i-1}) + 1 - I), tr = thr - f (threshold for the
-        // coordinate without f), vlast = coordinate (with f) of the block's last sample
-        int I[PIX];
-        float thr[PIX], f[PIX], tr[PIX], vlast[PIX];
+        // per pixel: I = integer anchor of the block, jdone = last grid point reached
+        // so far (absolute), vlast = coordinate (with f) of the block's last sample
+        int I[PIX], jdone[PIX];
+        float vlast[PIX];
         for (int q = 0; q < PIX; ++q) {
             // exact bins of the first and last samples: the half-open interval of
             // Algorithm 2 makes these the only samples where a one-bin rounding flip
             // changes the record by a whole sample
             const int64_t m = (act >> q & 1u) ? pix0 + q * kMixThreads + threadIdx.x : 0;
             const double nx = p.n_hat[3 * m], ny = p.n_hat[3 * m + 1], nz = p.n_hat[3 * m + 2];
-            thr[q] = (float)(exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu) + 1);
+            jdone[q] = exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu);
             s_jlast[wslot + lane * PIX + q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
             I[q] = 0;
             vlast[q] = 0.0f;
@@ -440,11 +460,15 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
                 s_anch[7] = Z.lo;
             }
             __syncthreads();
-            float v0p[PIX];   // coordinate (with f) of sample i0-1 relative to this anchor
+            const bool last_block = (i0 + n == p.ns1);
+            const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
+            int K[PIX], big[PIX];
+            int tot = 0;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
+                const int sl = wslot + lane * PIX + q;
                 // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
-                const float* w = s_w[wslot + lane * PIX + q];
+                const float* w = s_w[sl];
                 float s = s_anch[0], e = s_anch[1];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -462,89 +486,64 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
                 s = fminf(fmaxf(s, -1.0e9f), 1.0e9f);
                 const float Is = floorf(s);
                 const int Inew = (int)Is;
-                f[q] = __fadd_rn(__fsub_rn(s, Is), e);
-                v0p[q] = __fadd_rn(vlast[q], (float)(I[q] - Inew));   // rebase sample i0-1
-                thr[q] = (act >> q & 1u) ? thr[q] + (float)(I[q] - Inew) : INFINITY;
-                tr[q] = thr[q] - f[q];
+                const float f = __fadd_rn(__fsub_rn(s, Is), e);
+                const float v0p = __fadd_rn(vlast[q], (float)(I[q] - Inew));   // sample i0-1
                 I[q] = Inew;
+                const float xe = coord(s_dw[sl], s_scan[n - 1]);
+                const int jend = last_block ? s_jlast[sl] : Inew + last_point(xe, f);
+                int ja = jdone[q] + 1, jz = jend, kq = 0;
+                if ((act >> q & 1u) && jz >= ja && n > lo0) {
+                    if (ja < 0) {
+                        ja = 0;
+                        bits |= LW_ST_CLIP;
+                    }
+                    if (jz > nb - 1) {
+                        jz = nb - 1;
+                        bits |= LW_ST_CLIP;
+                    }
+                    kq = max(0, jz - ja + 1);
+                }
+                if (jend > jdone[q]) jdone[q] = jend;
+                vlast[q] = __fadd_rn(xe, f);
+                s_job[sl] = make_int4(Inew, ja, __float_as_int(f), __float_as_int(v0p));
+                big[q] = kq > kMaxWarpJobs ? kq : 0;
+                K[q] = kq > kMaxWarpJobs ? 0 : kq;
+                tot += K[q];
             }
-            // record a crossing of pixel q at staged step qq (coordinate v, previous vp)
-            auto cross = [&](int q, int qq, float v, float vp, int jnew) {
-                int ja = (int)thr[q] + I[q], jz = jnew;
-                if (ja < 0) {
-                    ja = 0;
-                    bits |= LW_ST_CLIP;
-                }
-                if (jz > nb - 1) {
-                    jz = nb - 1;
-                    bits |= LW_ST_CLIP;
-                }
-                if (ja <= jz) {
-                    const int cnt = jz - ja + 1;
-                    const float a0 = __fsub_rn((float)(ja - I[q]), vp);
-                    const float du = __fsub_rn(v, vp);
-                    if (cnt <= kMaxEventBins) {
-                        Event ev;
-                        ev.packed = (unsigned)(lane * PIX + q) | ((unsigned)qq << 7) |
-                                    ((unsigned)cnt << 17);
-                        ev.ja = ja;
-                        ev.a0 = a0;
-                        ev.du = du;
-                        myq[nq++] = ev;
-                    } else {   // a step spanning more grid points than an event holds
-                        deposit(pix0 + q * kMixThreads + threadIdx.x, qq, ja, cnt, a0, du);
-                    }
-                }
-                thr[q] = (float)(jnew + 1 - I[q]);
-                tr[q] = thr[q] - f[q];
-            };
-            const bool last_block = (i0 + n == p.ns1);
-            const int qend = last_block ? n - 1 : n;   // the last sample is peeled below
-            int qq = (b == 0) ? 1 : 0;                  // sample 0 only fills the buffer
-            while (true) {
-                for (; qq < qend; ++qq) {
-                    if (__any_sync(0xffffffffu, nq > kLaneQ - PIX)) break;
-                    const float4 sc = s_scan[qq];
-                    float v[PIX];
-                    bool any = false;
+            // the warp's grid points, one per lane and round
+            int incl = tot;
 #pragma unroll
-                    for (int q = 0; q < PIX; ++q) {
-                        v[q] = coord<PIX>(dw, q, sc);
-                        any |= v[q] >= tr[q];
-                    }
-                    if (any) {
-                        const float4 sp = s_scan[qq > 0 ? qq - 1 : 0];
-#pragma unroll
-                        for (int q = 0; q < PIX; ++q) {
-                            if (v[q] >= tr[q]) {
-                                const float vf = v[q] + f[q];
-                                const float vp = qq > 0 ? coord<PIX>(dw, q, sp) + f[q] : v0p[q];
-                                cross(q, qq, vf, vp, I[q] + (int)floorf(vf));
-                            }
-                        }
-                    }
-                }
-                drain();
-                if (qq >= qend) break;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
             }
-            if (last_block) {   // exact bin of the last sample (queue is empty here)
-                const int qq = n - 1;
-                const float4 sc = s_scan[qq];
-                const float4 sp = s_scan[qq > 0 ? qq - 1 : 0];
+            const int T = __shfl_sync(0xffffffffu, incl, 31);
+            int run = incl - tot;
 #pragma unroll
-                for (int q = 0; q < PIX; ++q) {
-                    const int jl = s_jlast[wslot + lane * PIX + q];
-                    if ((act >> q & 1u) && jl + 1 - I[q] > (int)thr[q]) {
-                        const float v = coord<PIX>(dw, q, sc) + f[q];
-                        const float vp = qq > 0 ? coord<PIX>(dw, q, sp) + f[q] : v0p[q];
-                        cross(q, qq, v, vp, jl);
+            for (int q = 0; q < PIX; ++q) {
+                s_kp[wslot + lane * PIX + q] = run;
+                run += K[q];
+            }
+            __syncwarp();
+            for (int t0 = 0; t0 < T; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < T) {
+                    int lo = 0, hi = 32 * PIX - 1;   // last slot whose offset is <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_kp[wslot + mid] <= t)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
                     }
+                    const int sl = wslot + lo;
+                    job(sl, s_job[sl].y + (t - s_kp[sl]), lo0, n);
                 }
-                drain();
-            } else {
-                const float4 sc = s_scan[n - 1];
+            }
 #pragma unroll
-                for (int q = 0; q < PIX; ++q) vlast[q] = coord<PIX>(dw, q, sc) + f[q];
+            for (int q = 0; q < PIX; ++q) {   // runs too long for the warp's job count
+                const int sl = wslot + lane * PIX + q;
+                for (int t = 0; t < big[q]; ++t) job(sl, s_job[sl].y + t, lo0, n);
             }
         }
     }
@@ -552,7 +551,7 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
 }
 
 template <int PIX, bool KAHAN>
-__global__ void __launch_bounds__(kMixThreads, 5) deposit_mixed_kernel(DepositArgs p) {
+__global__ void __launch_bounds__(kMixThreads, 4) deposit_mixed_kernel(DepositArgs p) {
     const int bits = mixed_cta<PIX, KAHAN>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
 }
@@ -567,7 +566,7 @@ struct BatchUnit {
 };
 
 template <int PIX, bool KAHAN>
-__global__ void __launch_bounds__(kMixThreads, 5)
+__global__ void __launch_bounds__(kMixThreads, 4)
     deposit_batched_kernel(const DepositArgs* __restrict__ vars,
                            const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
@@ -643,6 +642,7 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     a.n_blocks = traj->n_blocks;
     a.input_status = traj->input_status;
     a.ends = traj->ends;
+    a.order = traj->order;
     a.n_hat = det->n_hat;
     a.n_pix = det->n_pix;
     a.R = det->R > 0.0 ? det->R : 1.0;
@@ -663,7 +663,10 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     }
     constexpr int PIX = 4;
     const int64_t tiles = (det->n_pix + kMixThreads * PIX - 1) / (kMixThreads * PIX);
-    a.e_chunk = pick_chunk(traj->n_e, tiles);
+    // one electron per CTA row (as few as the grid's y limit allows), CTAs dispatched
+    // tile-fastest: the electrons in flight are consecutive in arrival order, so the
+    // record bins they update stay few enough to be served from L2
+    a.e_chunk = (int)std::max<int64_t>(1, (traj->n_e + 65534) / 65535);
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
     const size_t smem = sizeof(float4) * traj->block + sizeof(float) * 6 * (traj->block + 1);
     // static queues + dynamic staging exceed the 48 KB default: opt in
@@ -740,6 +743,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
         a.n_blocks = it.traj->n_blocks;
         a.input_status = it.traj->input_status;
         a.ends = it.traj->ends;
+        a.order = it.traj->order;
         a.n_hat = it.det->n_hat;
         a.n_pix = it.det->n_pix;
         a.R = it.det->R > 0.0 ? it.det->R : 1.0;

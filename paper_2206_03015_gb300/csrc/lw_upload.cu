@@ -12,14 +12,19 @@
 // lw_grid_bounds evaluates Eqs. (tu_min) and (tu_max).
 #include <math.h>
 
+#include <algorithm>
+
 #include "lw_internal.cuh"
 
 namespace lw {
 namespace {
 
+// Buckets of the electron ordering (light-front time of the first sample).
+constexpr int kOrderBuckets = 4096;
+
 struct TrajLayout {
     size_t status = 0, ends = 0, t = 0, r = 0, beta = 0, beta_dot = 0, scan = 0, field = 0,
-           anchor = 0;
+           anchor = 0, order = 0, order_tmp = 0;
     size_t total = 0;
     int64_t n_t = 0;
     int n_blocks = 0;
@@ -52,74 +57,66 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
         off = align256(off + sizeof(float) * 6 * (size_t)(n_e * ns1));
         L.anchor = off;
         off = align256(off + sizeof(D4) * (size_t)(n_e * L.n_blocks));
+        L.order = off;
+        off = align256(off + sizeof(int32_t) * (size_t)n_e);
+        L.order_tmp = off;   // two ordered keys (range) + kOrderBuckets counters
+        off = align256(off + 2 * sizeof(unsigned long long) + sizeof(int32_t) * kOrderBuckets);
     }
     L.total = off;
     return L;
 }
 
-// Input checks of every sample: finite values, |beta| < 1 (evaluated as
-// ((bx*bx + by*by) + bz*bz) < 1), strictly increasing lab time.
-__global__ void check_inputs_kernel(const double* __restrict__ t, int t_per_e,
-                                    const double* __restrict__ r,
-                                    const double* __restrict__ beta,
-                                    const double* __restrict__ bdot, int64_t n_e, int64_t ns1,
-                                    int32_t* __restrict__ status) {
-    const int64_t total = n_e * ns1;
+// One pass over the samples (grid: x = samples of an electron, y = electrons):
+// input checks of every sample -- finite values, |beta| < 1 (evaluated as
+// ((bx*bx + by*by) + bz*bz) < 1), strictly increasing lab time -- and, when
+// `scan` is non-null, the mixed section (block-relative float4, six field
+// floats, per-block FP64 anchor).  Reading each sample once serves both.
+__global__ void prepare_kernel(const double* __restrict__ t, int t_per_e,
+                               const double* __restrict__ r, const double* __restrict__ beta,
+                               const double* __restrict__ bdot, int64_t n_e, int ns1,
+                               int block_shift, int n_blocks, float4* __restrict__ scan,
+                               float* __restrict__ field, D4* __restrict__ anchor,
+                               int32_t* __restrict__ status) {
     int bits = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = s / ns1;
-        const int64_t i = s - k * ns1;
-        const double* x = r + 3 * s;
-        const double* b = beta + 3 * s;
-        const double* a = bdot + 3 * s;
-        bool fin = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(b[0]) &&
-                   isfinite(b[1]) && isfinite(b[2]) && isfinite(a[0]) && isfinite(a[1]) &&
-                   isfinite(a[2]);
-        if (!fin) bits |= LW_ST_NONFINITE;
-        double b2 = __dadd_rn(__dadd_rn(__dmul_rn(b[0], b[0]), __dmul_rn(b[1], b[1])),
-                              __dmul_rn(b[2], b[2]));
-        if (!(b2 < 1.0)) bits |= LW_ST_BETA;
-        if (t_per_e || k == 0) {
-            const double* tk = t + (t_per_e ? k * ns1 : 0);
-            if (!isfinite(tk[i])) bits |= LW_ST_NONFINITE;
-            if (i > 0 && !(tk[i] > tk[i - 1])) bits |= LW_ST_TIME;
+    for (int64_t k = blockIdx.y; k < n_e; k += gridDim.y) {
+        const double* tk = t + (t_per_e ? k * ns1 : 0);
+        const bool check_t = t_per_e || k == 0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns1; i += gridDim.x * blockDim.x) {
+            const int64_t s = k * ns1 + i;
+            const double x = r[3 * s], y = r[3 * s + 1], z = r[3 * s + 2];
+            const double* b = beta + 3 * s;
+            const double* a = bdot + 3 * s;
+            const double b0 = b[0], b1 = b[1], b2 = b[2];
+            const double a0 = a[0], a1 = a[1], a2 = a[2];
+            const double ti = tk[i];
+            const bool fin = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(b0) &&
+                             isfinite(b1) && isfinite(b2) && isfinite(a0) && isfinite(a1) &&
+                             isfinite(a2) && isfinite(ti);
+            if (!fin) bits |= LW_ST_NONFINITE;
+            const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
+                                        __dmul_rn(b2, b2));
+            if (!(bb < 1.0)) bits |= LW_ST_BETA;
+            if (check_t && i > 0 && !(ti > tk[i - 1])) bits |= LW_ST_TIME;
+            if (scan) {
+                const int ib = (i >> block_shift) << block_shift;
+                const int64_t sb = k * ns1 + ib;
+                const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
+                const double tau = ti - z * kInvC0;
+                const double taub = tk[ib] - zb * kInvC0;
+                scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
+                                      (float)(z - zb));
+                float* f = field + 6 * s;
+                f[0] = (float)b0;
+                f[1] = (float)b1;
+                f[2] = (float)(1.0 - b2);
+                f[3] = (float)a0;
+                f[4] = (float)a1;
+                f[5] = (float)a2;
+                if (i == ib) anchor[k * n_blocks + (i >> block_shift)] = D4{taub, xb, yb, zb};
+            }
         }
     }
     block_status_or(status, bits);
-}
-
-__global__ void build_mixed_kernel(const double* __restrict__ t, int t_per_e,
-                                   const double* __restrict__ r,
-                                   const double* __restrict__ beta,
-                                   const double* __restrict__ bdot, int64_t n_e, int64_t ns1,
-                                   int block, int n_blocks, float4* __restrict__ scan,
-                                   float* __restrict__ field, D4* __restrict__ anchor) {
-    const int64_t total = n_e * ns1;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = s / ns1;
-        const int64_t i = s - k * ns1;
-        const int64_t ib = (i / block) * block;
-        const int64_t sb = k * ns1 + ib;
-        const double* tk = t + (t_per_e ? k * ns1 : 0);
-        const double x = r[3 * s], y = r[3 * s + 1], z = r[3 * s + 2];
-        const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
-        const double tau = tk[i] - z * kInvC0;
-        const double taub = tk[ib] - zb * kInvC0;
-        scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
-                              (float)(z - zb));
-        const double* b = beta + 3 * s;
-        const double* a = bdot + 3 * s;
-        float* f = field + 6 * s;
-        f[0] = (float)b[0];
-        f[1] = (float)b[1];
-        f[2] = (float)(1.0 - b[2]);
-        f[3] = (float)a[0];
-        f[4] = (float)a[1];
-        f[5] = (float)a[2];
-        if (i == ib) anchor[k * n_blocks + i / block] = D4{taub, xb, yb, zb};
-    }
 }
 
 __global__ void ends_kernel(const double* __restrict__ t, int t_per_e,
@@ -139,6 +136,85 @@ __global__ void ends_kernel(const double* __restrict__ t, int t_per_e,
         e[5] = x1[0];
         e[6] = x1[1];
         e[7] = x1[2];
+    }
+}
+
+// Electron ordering for the mixed deposit: electrons sorted (by buckets of
+// 1/kOrderBuckets of the range) on the light-front time tau = t - z/c0 of their
+// first sample, which orders their arrival at detectors near the z axis.  The
+// deposit visits electrons in this order, so the electrons in flight at any
+// time update a narrow band of observer bins.
+__device__ __forceinline__ double first_tau(const double* e) { return e[0] - e[3] * kInvC0; }
+
+__global__ void order_range_kernel(const double* __restrict__ ends, int64_t n_e,
+                                   unsigned long long* keys) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = first_tau(ends + 8 * k);
+        if (isfinite(v)) {
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&keys[0], ordered_key(lo));
+        atomicMax(&keys[1], ordered_key(hi));
+    }
+}
+
+__device__ __forceinline__ int order_bucket(const double* e, const unsigned long long* keys) {
+    const double lo = key_to_double(keys[0]), hi = key_to_double(keys[1]);
+    const double v = first_tau(e);
+    if (!(hi > lo) || !isfinite(v)) return 0;
+    const double x = (v - lo) / (hi - lo) * kOrderBuckets;
+    return (int)fmin(fmax(x, 0.0), (double)(kOrderBuckets - 1));
+}
+
+__global__ void order_count_kernel(const double* __restrict__ ends, int64_t n_e,
+                                   const unsigned long long* __restrict__ keys,
+                                   int32_t* __restrict__ counts) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
+         k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&counts[order_bucket(ends + 8 * k, keys)], 1);
+}
+
+// Exclusive prefix sum of the bucket counts, in place (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) order_scan_kernel(int32_t* counts) {
+    constexpr int kPer = kOrderBuckets / 1024;
+    __shared__ int32_t s_sum[1024];
+    int32_t v[kPer];
+    int32_t sum = 0;
+    for (int i = 0; i < kPer; ++i) {
+        v[i] = counts[threadIdx.x * kPer + i];
+        sum += v[i];
+    }
+    s_sum[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {   // Hillis-Steele inclusive scan of the sums
+        const int32_t add = threadIdx.x >= d ? s_sum[threadIdx.x - d] : 0;
+        __syncthreads();
+        s_sum[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int32_t run = s_sum[threadIdx.x] - sum;
+    for (int i = 0; i < kPer; ++i) {
+        counts[threadIdx.x * kPer + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void order_scatter_kernel(const double* __restrict__ ends, int64_t n_e,
+                                     const unsigned long long* __restrict__ keys,
+                                     int32_t* __restrict__ offsets, int32_t* __restrict__ order) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(&offsets[order_bucket(ends + 8 * k, keys)], 1);
+        order[pos] = (int32_t)k;
     }
 }
 
@@ -199,6 +275,7 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
                                       void* ws, size_t* ws_bytes, lw_traj* out, void* stream) {
     if (!in || !ws_bytes || !out) return LW_EINVAL;
     if (in->n_e < 1 || in->n_s < 1) return LW_EINVAL;
+    if (in->n_s >= (int64_t(1) << 30) || in->n_e >= (int64_t(1) << 31)) return LW_EUNSUPPORTED;
     if (!in->t || !in->r || !in->beta || !in->beta_dot) return LW_EINVAL;
     if (sections <= 0 || (sections & ~(LW_SECTION_FP64 | LW_SECTION_MIXED))) return LW_EINVAL;
     if (block == 0) block = 128;
@@ -257,19 +334,38 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
                                                                  ends);
     if (launch_status() != LW_OK) return LW_ECUDA;
     v.ends = ends;
-    check_inputs_kernel<<<grid_for(in->n_e * ns1, threads), threads, 0, st>>>(
-        t, t_per_e, r, beta, bdot, in->n_e, ns1, status);
-    if (launch_status() != LW_OK) return LW_ECUDA;
+    float4* scan = nullptr;
+    float* field = nullptr;
+    D4* anchor = nullptr;
     if (sections & LW_SECTION_MIXED) {
-        float4* scan = reinterpret_cast<float4*>(base + L.scan);
-        float* field = reinterpret_cast<float*>(base + L.field);
-        D4* anchor = reinterpret_cast<D4*>(base + L.anchor);
-        build_mixed_kernel<<<grid_for(in->n_e * ns1, threads), threads, 0, st>>>(
-            t, t_per_e, r, beta, bdot, in->n_e, ns1, block, L.n_blocks, scan, field, anchor);
-        if (launch_status() != LW_OK) return LW_ECUDA;
+        scan = reinterpret_cast<float4*>(base + L.scan);
+        field = reinterpret_cast<float*>(base + L.field);
+        anchor = reinterpret_cast<D4*>(base + L.anchor);
         v.scan = scan;
         v.field = field;
         v.anchor = reinterpret_cast<const double*>(anchor);
+    }
+    int shift = 0;
+    while ((1 << shift) < block) ++shift;
+    const dim3 g((unsigned)std::min<int64_t>((ns1 + threads - 1) / threads, 1024),
+                 (unsigned)std::min<int64_t>(in->n_e, 65535));
+    prepare_kernel<<<g, threads, 0, st>>>(t, t_per_e, r, beta, bdot, in->n_e, (int)ns1, shift,
+                                          L.n_blocks, scan, field, anchor, status);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    if (sections & LW_SECTION_MIXED) {
+        int32_t* order = reinterpret_cast<int32_t*>(base + L.order);
+        unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + L.order_tmp);
+        int32_t* counts = reinterpret_cast<int32_t*>(keys + 2);
+        if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * kOrderBuckets, st) != cudaSuccess)
+            return LW_ECUDA;
+        bounds_init_kernel<<<1, 1, 0, st>>>(keys);
+        const int ge = grid_for(in->n_e, threads);
+        order_range_kernel<<<ge, threads, 0, st>>>(ends, in->n_e, keys);
+        order_count_kernel<<<ge, threads, 0, st>>>(ends, in->n_e, keys, counts);
+        order_scan_kernel<<<1, 1024, 0, st>>>(counts);
+        order_scatter_kernel<<<ge, threads, 0, st>>>(ends, in->n_e, keys, counts, order);
+        if (launch_status() != LW_OK) return LW_ECUDA;
+        v.order = order;
     }
     *out = v;
     *ws_bytes = L.total;

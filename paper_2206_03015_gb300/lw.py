@@ -50,7 +50,8 @@ class lw_traj(ctypes.Structure):
                 ("t", ctypes.c_void_p), ("r", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("beta_dot", ctypes.c_void_p), ("scan", ctypes.c_void_p),
                 ("field", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
-                ("ends", ctypes.c_void_p), ("input_status", ctypes.c_void_p)]
+                ("ends", ctypes.c_void_p), ("input_status", ctypes.c_void_p),
+                ("order", ctypes.c_void_p)]
 
 
 class lw_batch(ctypes.Structure):
@@ -219,6 +220,14 @@ class Trajectories:
     @property
     def n_s(self):
         return self.view.n_s
+
+    def order(self):
+        """The electron visiting order of the mixed deposit (int32 [n_e] view into the
+        workspace), or None without the mixed section."""
+        if not self.view.order:
+            return None
+        off = self.view.order - self.ws.data_ptr()
+        return self.ws[off:off + 4 * self.n_e].view(torch.int32)
 
 
 def _as_input(x, device):

@@ -149,3 +149,22 @@ def test_status_word_reports_bad_inputs():
     for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN):
         g = gpu_run(bad, n_hat, grid, prec, spectrum=False)
         assert g["status"] & lw.LW_ST_BETA and g["status"] & lw.LW_ST_TIME
+
+
+def test_upload_orders_electrons_by_first_light_front_time():
+    """The mixed section's electron order is a permutation sorted by buckets of
+    1/4096 of the range of tau = t - z/c0 at the first sample."""
+    tr = simple.random_smooth(300, 40, 2e-18, 61, gamma=8.0, amp=0.3)
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot)
+    order = traj.order().cpu().numpy()
+    assert np.array_equal(np.sort(order), np.arange(tr.n_e))
+    t0 = tr.t[0] if tr.t.ndim == 1 else tr.t[:, 0]
+    tau = t0 - tr.r[:, 0, 2] * (1.0 / 299792458.0)
+    lo, hi = tau.min(), tau.max()
+    bucket = np.minimum(((tau - lo) / (hi - lo) * 4096).astype(np.int64), 4095)
+    # the device may round tau differently by an ulp (FMA), moving a key across a
+    # bucket edge: allow one bucket of disorder, nothing more
+    assert np.all(np.diff(bucket[order]) >= -1)
+    assert np.mean(np.diff(bucket[order]) >= 0) > 0.99
+    assert lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
+                                      sections=lw.LW_SECTION_FP64).order() is None
