@@ -530,7 +530,7 @@ def main():
     ap.add_argument("--n-s", type=int, default=10_000)
     ap.add_argument("--nx", type=int, default=64)
     ap.add_argument("--n-bins", type=int, default=65_536)
-    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--block", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -146,7 +146,7 @@ typedef struct {
  * position, velocity and acceleration per particle; here for every step).
  *   sections   LW_SECTION_FP64 and/or LW_SECTION_MIXED
  *   block      samples per anchoring block of the mixed section (16..1024,
- *              power of two; 0 = default 128)
+ *              power of two; 0 = default 512)
  *   ws         device workspace, 256-byte aligned; NULL = size query
  *   ws_bytes   in: size of ws; out: bytes required
  *   out        filled with the device view on success

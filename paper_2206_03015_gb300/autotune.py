@@ -16,7 +16,7 @@ import torch
 
 from . import lw
 
-BLOCKS = (64, 128, 256)
+BLOCKS = (128, 256, 512)
 CHUNKS = (1, 2, 4, 8, 16, 32)
 
 

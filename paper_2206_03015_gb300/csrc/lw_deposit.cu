@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_kernel(DepositArgs 
 
 // ------------------------------------------------------------------ mixed
 
-constexpr int kMixThreads = 128;
+constexpr int kMixThreads = 256;
+constexpr int kMixPix = 2;            // pixels per thread: tiles of 512 pixels
+constexpr int kMixMinBlocks = 3;      // resident CTAs per SM the register budget allows
 
 struct DF {   // unevaluated sum hi + lo of two floats
     float hi, lo;
@@ -237,7 +239,7 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __
     F[0] = F[1] = F[2] = 0.0f;
     if (!(D > 0.0f)) return;
     const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
-    const float invD = 1.0f / D;
+    const float invD = __frcp_rn(D);
     const float invD3 = invD * invD * invD;
     if (flags & LW_FIELD_ACCEL) {
         const float na = fmaf(pc.nz, az, fmaf(pc.ny, ay, pc.nx * ax));
@@ -257,6 +259,9 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __
 // Grid points of one pixel and block above which the owning lane deposits them
 // itself instead of handing them to the warp (keeps the warp's job count in int).
 constexpr int kMaxWarpJobs = 1 << 20;
+// Jobs of a warp and block listed explicitly (slot, grid point); later ones are
+// located by bisection over the slots' job offsets.
+constexpr int kJobTable = 128;
 
 template <bool KAHAN>
 __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
@@ -276,11 +281,11 @@ __device__ __forceinline__ int exact_bin(const double* e, double nx, double ny, 
     return (int)floor(u);
 }
 
-// Bin coordinate of a staged sample relative to the block anchor, without the
-// anchor fraction f: sc.x holds C = s*dtau + w_c . dr for the CTA's reference
-// slope w_c, dw = w_pixel - w_c, so u - I - f = C + dw . dr.
-__device__ __forceinline__ float coord(float4 dw, float4 sc) {
-    return fmaf(dw.z, sc.w, fmaf(dw.y, sc.z, fmaf(dw.x, sc.y, sc.x)));
+// Bin coordinate of a staged sample relative to its block's anchor, without the
+// anchor fraction f: u - I - f = s dtau + w . dr, with sc = (dtau, dr) and
+// w = (w_x, w_y, w_z) the pixel's slope (FP32 hi parts), s = 1/dt_u.
+__device__ __forceinline__ float coord(float4 w, float s, float4 sc) {
+    return fmaf(w.z, sc.w, fmaf(w.y, sc.z, fmaf(w.x, sc.y, s * sc.x)));
 }
 
 // Grid point J (relative to the anchor integer) is reached by a sample of
@@ -296,6 +301,29 @@ __device__ __forceinline__ int last_point(float x, float f) {
     return J;
 }
 
+// Asynchronous global -> shared copies (LDGSTS): the next block of samples is
+// staged while the current one is processed.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// One staging buffer: B float4 samples and B+1 field records (the block's
+// samples preceded by the previous block's last one).
+__host__ __device__ constexpr size_t stage_bytes(int B) {
+    return (16 * (size_t)B + 24 * ((size_t)B + 1) + 31) / 32 * 32;
+}
+
 // The work of one CTA: pixel tile `tile` (kMixThreads * PIX pixels) and electron
 // chunk `chunk` (p.e_chunk electrons) of one variant.  Returns the status bits.
 //
@@ -308,30 +336,30 @@ __device__ __forceinline__ int last_point(float x, float f) {
 // evaluates one coordinate per pixel; the grid points of the warp's 128
 // pixels are then spread over its 32 lanes (prefix sum of the runs, one grid
 // point per lane and round), each lane finding its step, evaluating the two
-// fields and adding the interpolated value.
+// fields and adding the interpolated value.  Blocks are staged into two
+// alternating shared buffers by asynchronous copies, one block ahead.
 template <int PIX, bool KAHAN>
 __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     constexpr int kSlots = kMixThreads * PIX;
     const int B = p.block;
-    float4* s_scan = smem4;                                    // [B] (C, dx, dy, dz)
-    float* s_field = reinterpret_cast<float*>(smem4 + B);      // [B+1][6], sample i0-1 first
-    __shared__ float s_anch[8];                                // T, R_x, R_y, R_z (hi, lo)
-    __shared__ float s_wc[3];                                  // reference slope of the CTA
-    __shared__ float s_w[kSlots][6];                           // slopes: hi parts, lo parts
-    __shared__ float4 s_dw[kSlots];                            // slope - reference slope
-    __shared__ float4 s_pc[kSlots];                            // n_x, n_y, n_z, 1 - n_z (FP32)
+    const size_t sbytes = stage_bytes(B);
+    constexpr int kWarpsMix = kMixThreads / 32;
+    __shared__ float4 s_wh[kSlots];                            // slope hi parts (w_x, w_y, w_z)
     __shared__ int4 s_job[kSlots];                             // block: I, first point, f, v_prev
+    __shared__ float s_xe[kSlots];                             // block: coordinate of last sample
     __shared__ int s_kp[kSlots];                               // block: job offset in the warp
-    __shared__ int s_jlast[kSlots];                            // exact bin of the last sample
+    __shared__ int2 s_tab[kWarpsMix][kJobTable];               // block: (slot, grid point) of job t
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wslot = warp * 32 * PIX;
     const float s32 = (float)p.inv_dtu;
     const float c0_over_R = (float)(kC0 / p.R);
+    const float inv_sc = (float)(kC0 * p.dt_u);   // direction from slope: n_x = -w_x c0 dt_u
     const int nb = (int)p.n_bins;
     const int64_t pix0 = tile * kSlots;
     unsigned act = 0;
+    float wlo[PIX][3];   // slope lo parts of this thread's pixels (its anchors only)
     __syncthreads();   // shared arrays may still be read by the previous unit
     for (int q = 0; q < PIX; ++q) {
         const int64_t m = pix0 + q * kMixThreads + threadIdx.x;
@@ -342,32 +370,19 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
             ny = p.n_hat[3 * m + 1];
             nz = p.n_hat[3 * m + 2];
         }
-        const double omnz = (nx * nx + ny * ny) / (1.0 + nz);   // 1 - n_z without cancellation
+        // 1 - n_z: its FP64 cancellation error (<= 2^-53 absolute) moves the anchor by
+        // 2^-53 |z_b| / (c0 dt_u) bins, below 1e-8 while |z_b| < 1e8 c0 dt_u -- far
+        // below the FP32 coordinate's own rounding
+        const double omnz = 1.0 - nz;
         const double sc = kInvC0 * p.inv_dtu;
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
         const int sl = wslot + lane * PIX + q;
-        float* w = s_w[sl];
-        w[0] = wx.hi;
-        w[1] = wy.hi;
-        w[2] = wz.hi;
-        w[3] = wx.lo;
-        w[4] = wy.lo;
-        w[5] = wz.lo;
-        s_pc[sl] = make_float4((float)nx, (float)ny, (float)nz, (float)omnz);
-        if (threadIdx.x == 0 && q == 0) {
-            s_wc[0] = wx.hi;
-            s_wc[1] = wy.hi;
-            s_wc[2] = wz.hi;
-        }
+        s_wh[sl] = make_float4(wx.hi, wy.hi, wz.hi, 0.0f);
+        wlo[q][0] = wx.lo;
+        wlo[q][1] = wy.lo;
+        wlo[q][2] = wz.lo;
     }
-    __syncthreads();
-    for (int q = 0; q < PIX; ++q) {
-        const int sl = wslot + lane * PIX + q;
-        s_dw[sl] = make_float4(s_w[sl][0] - s_wc[0], s_w[sl][1] - s_wc[1], s_w[sl][2] - s_wc[2],
-                               0.0f);
-    }
-    const float wcx = s_wc[0], wcy = s_wc[1], wcz = s_wc[2];
     int bits = 0;
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
 
@@ -376,52 +391,54 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
         const int w = sl / (32 * PIX), r = sl % (32 * PIX);
         return pix0 + (r % PIX) * kMixThreads + w * 32 + r / PIX;
     };
-    // deposit grid point j (absolute) of slot `sl` in the staged block of n samples;
-    // lo0 = first sample that may end a step (1 in the trajectory's first block)
-    auto job = [&](int sl, int j, int lo0, int n) {
-        const int4 jb = s_job[sl];
-        const float f = __int_as_float(jb.z);
-        const float4 dw = s_dw[sl];
-        const float J = (float)(j - jb.x);
-        const float tJ = __fsub_rn(J, f);
-        int lo = lo0, hi = n - 1;   // first sample reaching tJ; the last one if none does
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (coord(dw, s_scan[mid]) >= tJ)
-                hi = mid;
-            else
-                lo = mid + 1;
+    auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
+    // stage block b of electron k into buffer `buf`
+    auto issue = [&](int64_t k, int b, int buf) {
+        unsigned char* base = smem_raw + buf * sbytes;
+        float4* ss = reinterpret_cast<float4*>(base);
+        float2* sf = reinterpret_cast<float2*>(base + 16 * (size_t)B);
+        const int64_t i0 = (int64_t)b * B;
+        const int n = (int)min((int64_t)B, p.ns1 - i0);
+        const float4* src = p.scan + k * p.ns1 + i0;
+        for (int q = threadIdx.x; q < n; q += kMixThreads) cp_async16(ss + q, src + q);
+        // field records of samples i0-1 .. i0+n-1 (3 float2 each); the first block has
+        // no previous sample and leaves that record unset (no step ends at sample 0)
+        const float2* fsrc = reinterpret_cast<const float2*>(p.field + 6 * (k * p.ns1 + i0));
+        for (int q = (b == 0 ? 3 : 0) + threadIdx.x; q < 3 * (n + 1); q += kMixThreads)
+            cp_async8(sf + q, fsrc + (q - 3));
+        cp_async_commit();
+    };
+    // FP32 pairs of block b's anchor (T = (tau_b - t_min)/dt_u, x_b, y_b, z_b): lane l of
+    // every warp splits the anchors of blocks 32c + l at once, one FP64 pass per 32 blocks
+    auto split_anchor = [&](int64_t k, int b, float (&an)[8]) {
+        if (b < p.n_blocks) {
+            const D4 a = p.anchor[k * p.n_blocks + b];
+            const DF T = split_double((a.x - p.t_min) * p.inv_dtu);
+            const DF X = split_double(a.y), Y = split_double(a.z), Z = split_double(a.w);
+            an[0] = T.hi;
+            an[1] = T.lo;
+            an[2] = X.hi;
+            an[3] = X.lo;
+            an[4] = Y.hi;
+            an[5] = Y.lo;
+            an[6] = Z.hi;
+            an[7] = Z.lo;
         }
-        const float vi = __fadd_rn(coord(dw, s_scan[lo]), f);
-        const float vp = lo > 0 ? __fadd_rn(coord(dw, s_scan[lo - 1]), f) : __int_as_float(jb.w);
-        const float a0 = __fsub_rn(J, vp);
-        const float du = __fsub_rn(vi, vp);
-        const float4 c = s_pc[sl];
-        const PixelConst pc{c.x, c.y, c.z, c.w};
-        float Fb[3], Fa[3];
-        field_fp32(pc, s_field + 6 * lo, p.flags, c0_over_R, Fb);
-        field_fp32(pc, s_field + 6 * (lo + 1), p.flags, c0_over_R, Fa);
-        const float inv_du = du > 0.0f ? 1.0f / du : 0.0f;
-        const float wb = a0 * inv_du;
-        const float wa = 1.0f - wb;
-        const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
-        accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
-        accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-        accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
     };
 
     const int64_t k0 = chunk * p.e_chunk;
     const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
+    int buf = 0;
+    if (k0 < k1) issue(electron(k0), 0, 0);
     for (int64_t kk = k0; kk < k1; ++kk) {
-        const int64_t k = p.order ? (int64_t)p.order[kk] : kk;
-        const float4* sck = p.scan + k * p.ns1;
-        const float* fdk = p.field + 6 * k * p.ns1;
-        const D4* anc = p.anchor + k * p.n_blocks;
+        const int64_t k = electron(kk);
         const double* ends = p.ends + 8 * k;
         // per pixel: I = integer anchor of the block, jdone = last grid point reached
-        // so far (absolute), vlast = coordinate (with f) of the block's last sample
-        int I[PIX], jdone[PIX];
+        // so far (absolute), jlast = exact bin of the last sample, vlast = coordinate
+        // (with f) of the block's last sample
+        int I[PIX], jdone[PIX], jlast[PIX];
         float vlast[PIX];
+        float anc32[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         for (int q = 0; q < PIX; ++q) {
             // exact bins of the first and last samples: the half-open interval of
             // Algorithm 2 makes these the only samples where a one-bin rounding flip
@@ -429,37 +446,27 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
             const int64_t m = (act >> q & 1u) ? pix0 + q * kMixThreads + threadIdx.x : 0;
             const double nx = p.n_hat[3 * m], ny = p.n_hat[3 * m + 1], nz = p.n_hat[3 * m + 2];
             jdone[q] = exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu);
-            s_jlast[wslot + lane * PIX + q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
+            jlast[q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
             I[q] = 0;
             vlast[q] = 0.0f;
         }
         for (int b = 0; b < p.n_blocks; ++b) {
             const int64_t i0 = (int64_t)b * B;
             const int n = (int)min((int64_t)B, p.ns1 - i0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < n; q += kMixThreads) {
-                float4 v = sck[i0 + q];
-                v.x = fmaf(wcz, v.w, fmaf(wcy, v.z, fmaf(wcx, v.y, s32 * v.x)));
-                s_scan[q] = v;
-            }
-            for (int q = threadIdx.x; q < 6 * (n + 1); q += kMixThreads) {
-                const int64_t idx = 6 * (i0 - 1) + q;
-                s_field[q] = (idx >= 0) ? fdk[idx] : 0.0f;
-            }
-            if (threadIdx.x == 0) {
-                const D4 a = anc[b];
-                const DF T = split_double((a.x - p.t_min) * p.inv_dtu);
-                const DF X = split_double(a.y), Y = split_double(a.z), Z = split_double(a.w);
-                s_anch[0] = T.hi;
-                s_anch[1] = T.lo;
-                s_anch[2] = X.hi;
-                s_anch[3] = X.lo;
-                s_anch[4] = Y.hi;
-                s_anch[5] = Y.lo;
-                s_anch[6] = Z.hi;
-                s_anch[7] = Z.lo;
-            }
-            __syncthreads();
+            cp_async_wait_all();
+            __syncthreads();   // block b staged; every warp is done with block b-1
+            if (b + 1 < p.n_blocks)
+                issue(k, b + 1, buf ^ 1);
+            else if (kk + 1 < k1)
+                issue(electron(kk + 1), 0, buf ^ 1);
+            const unsigned char* base = smem_raw + buf * sbytes;
+            const float4* s_scan = reinterpret_cast<const float4*>(base);
+            const float* s_field = reinterpret_cast<const float*>(base + 16 * (size_t)B);
+            buf ^= 1;
+            if ((b & 31) == 0) split_anchor(k, b + lane, anc32);
+            float an[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) an[c] = __shfl_sync(0xffffffffu, anc32[c], b & 31);
             const bool last_block = (i0 + n == p.ns1);
             const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
             int K[PIX], big[PIX];
@@ -468,14 +475,16 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
             for (int q = 0; q < PIX; ++q) {
                 const int sl = wslot + lane * PIX + q;
                 // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
-                const float* w = s_w[sl];
-                float s = s_anch[0], e = s_anch[1];
+                const float4 wh = s_wh[sl];
+                const float whc[3] = {wh.x, wh.y, wh.z};
+                const float wlc[3] = {wlo[q][0], wlo[q][1], wlo[q][2]};
+                float s = an[0], e = an[1];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float Rh = s_anch[2 + 2 * c], Rl = s_anch[3 + 2 * c];
-                    const float pr = __fmul_rn(w[c], Rh);
-                    float pe = fmaf(w[c], Rh, -pr);
-                    pe = fmaf(w[c], Rl, fmaf(w[3 + c], Rh, pe));
+                    const float Rh = an[2 + 2 * c], Rl = an[3 + 2 * c];
+                    const float pr = __fmul_rn(whc[c], Rh);
+                    float pe = fmaf(whc[c], Rh, -pr);
+                    pe = fmaf(whc[c], Rl, fmaf(wlc[c], Rh, pe));
                     const float s2 = __fadd_rn(s, pr);
                     const float bb = __fsub_rn(s2, s);
                     const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)),
@@ -489,8 +498,8 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
                 const float f = __fadd_rn(__fsub_rn(s, Is), e);
                 const float v0p = __fadd_rn(vlast[q], (float)(I[q] - Inew));   // sample i0-1
                 I[q] = Inew;
-                const float xe = coord(s_dw[sl], s_scan[n - 1]);
-                const int jend = last_block ? s_jlast[sl] : Inew + last_point(xe, f);
+                const float xe = coord(wh, s32, s_scan[n - 1]);
+                const int jend = last_block ? jlast[q] : Inew + last_point(xe, f);
                 int ja = jdone[q] + 1, jz = jend, kq = 0;
                 if ((act >> q & 1u) && jz >= ja && n > lo0) {
                     if (ja < 0) {
@@ -506,11 +515,13 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
                 if (jend > jdone[q]) jdone[q] = jend;
                 vlast[q] = __fadd_rn(xe, f);
                 s_job[sl] = make_int4(Inew, ja, __float_as_int(f), __float_as_int(v0p));
+                s_xe[sl] = xe;
                 big[q] = kq > kMaxWarpJobs ? kq : 0;
                 K[q] = kq > kMaxWarpJobs ? 0 : kq;
                 tot += K[q];
             }
-            // the warp's grid points, one per lane and round
+            // the warp's grid points: prefix sum of the runs over the warp's slots, and the
+            // first kJobTable of them listed as (slot, grid point) by their owners
             int incl = tot;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -521,37 +532,104 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
             int run = incl - tot;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
-                s_kp[wslot + lane * PIX + q] = run;
+                const int sl = wslot + lane * PIX + q;
+                s_kp[sl] = run;
+                const int ja = s_job[sl].y;
+                for (int t = 0; t < K[q] && run + t < kJobTable; ++t)
+                    s_tab[warp][run + t] = make_int2(sl, ja + t);
                 run += K[q];
             }
             __syncwarp();
-            for (int t0 = 0; t0 < T; t0 += 32) {
-                const int t = t0 + lane;
-                if (t < T) {
-                    int lo = 0, hi = 32 * PIX - 1;   // last slot whose offset is <= t
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_kp[wslot + mid] <= t)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
+            // slot of the warp's job t beyond the table: the last slot whose offset is <= t
+            auto slot_of = [&](int t) -> int {
+                int pos = 0;
+#pragma unroll
+                for (int step = 16 * PIX; step > 0; step >>= 1)
+                    if (s_kp[wslot + pos + step] <= t) pos += step;
+                return wslot + pos;
+            };
+            // Grid point j (absolute) of slot sl: its step ends at the first sample in
+            // [lo0, n-1] whose coordinate reaches fl(J - f), J = j - I (the last sample if
+            // none does, at the trajectory's exact end).  Search: the bracket (a, b]
+            // starts at the block's ends; probes alternate between linear interpolation
+            // of the coordinate (near-linear over a block) and bisection, and the final
+            // bracket's two coordinates are the ones the weights need.
+            auto job = [&](int sl, int j) {
+                const int4 jb = s_job[sl];
+                const float f = __int_as_float(jb.z);
+                const float v0p = __int_as_float(jb.w);
+                const float4 w = s_wh[sl];
+                const float J = (float)(j - jb.x);
+                const float tJ = __fsub_rn(J, f);
+                int a = lo0 - 1, hb = n - 1;
+                float xa = lo0 ? coord(w, s32, s_scan[0]) : __fsub_rn(v0p, f);
+                float xb = s_xe[sl];
+                if (xb < tJ) {   // beyond the FP32 coordinate of the last sample
+                    a = n - 2;
+                    if (a >= 0) xa = coord(w, s32, s_scan[a]);
+                } else {
+                    bool interp = true;
+                    while (hb - a > 1) {
+                        int g = (a + hb) >> 1;
+                        if (interp) {
+                            const float fr = __fdividef(tJ - xa, xb - xa);
+                            const float gf = ceilf(fr * (float)(hb - a));
+                            g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
+                        }
+                        interp = !interp;
+                        const float xg = coord(w, s32, s_scan[g]);
+                        if (xg >= tJ) {
+                            hb = g;
+                            xb = xg;
+                        } else {
+                            a = g;
+                            xa = xg;
+                        }
                     }
-                    const int sl = wslot + lo;
-                    job(sl, s_job[sl].y + (t - s_kp[sl]), lo0, n);
+                }
+                const int i = hb;
+                const float vi = __fadd_rn(xb, f);
+                const float vp = a >= 0 ? __fadd_rn(xa, f) : v0p;
+                const float a0 = __fsub_rn(J, vp);
+                const float du = __fsub_rn(vi, vp);
+                PixelConst pc;
+                pc.nx = -w.x * inv_sc;
+                pc.ny = -w.y * inv_sc;
+                pc.omnz = w.z * inv_sc;
+                pc.nz = 1.0f - pc.omnz;
+                float Fb[3], Fa[3];
+                field_fp32(pc, s_field + 6 * i, p.flags, c0_over_R, Fb);
+                field_fp32(pc, s_field + 6 * (i + 1), p.flags, c0_over_R, Fa);
+                const float wb = du > 0.0f ? a0 * __frcp_rn(du) : 0.0f;
+                const float wa = 1.0f - wb;
+                const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
+                accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
+                accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+                accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+            };
+            for (int t = lane; t < T; t += 32) {
+                if (t < kJobTable) {
+                    const int2 e = s_tab[warp][t];
+                    job(e.x, e.y);
+                } else {
+                    const int sl = slot_of(t);
+                    job(sl, s_job[sl].y + (t - s_kp[sl]));
                 }
             }
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {   // runs too long for the warp's job count
                 const int sl = wslot + lane * PIX + q;
-                for (int t = 0; t < big[q]; ++t) job(sl, s_job[sl].y + t, lo0, n);
+                for (int t = 0; t < big[q]; ++t) job(sl, s_job[sl].y + t);
             }
+            __syncwarp();   // s_job / s_kp are rewritten for the next block
         }
     }
+    cp_async_wait_all();
     return bits;
 }
 
 template <int PIX, bool KAHAN>
-__global__ void __launch_bounds__(kMixThreads, 4) deposit_mixed_kernel(DepositArgs p) {
+__global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
     const int bits = mixed_cta<PIX, KAHAN>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
 }
@@ -566,7 +644,7 @@ struct BatchUnit {
 };
 
 template <int PIX, bool KAHAN>
-__global__ void __launch_bounds__(kMixThreads, 4)
+__global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     deposit_batched_kernel(const DepositArgs* __restrict__ vars,
                            const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
@@ -661,15 +739,15 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
         deposit_fp64_kernel<<<g, kFp64Threads, 0, st>>>(a);
         return launch_status();
     }
-    constexpr int PIX = 4;
+    constexpr int PIX = kMixPix;
     const int64_t tiles = (det->n_pix + kMixThreads * PIX - 1) / (kMixThreads * PIX);
     // one electron per CTA row (as few as the grid's y limit allows), CTAs dispatched
     // tile-fastest: the electrons in flight are consecutive in arrival order, so the
     // record bins they update stay few enough to be served from L2
     a.e_chunk = (int)std::max<int64_t>(1, (traj->n_e + 65534) / 65535);
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
-    const size_t smem = sizeof(float4) * traj->block + sizeof(float) * 6 * (traj->block + 1);
-    // static queues + dynamic staging exceed the 48 KB default: opt in
+    const size_t smem = 2 * stage_bytes(traj->block);   // double-buffered staging
+    // static tables + double-buffered staging exceed the 48 KB default: opt in
     auto kern = precision == LW_MIXED_KAHAN ? deposit_mixed_kernel<PIX, true>
                                             : deposit_mixed_kernel<PIX, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -706,7 +784,7 @@ size_t batch_layout(int n_items, int64_t n_units, size_t* off_vars, size_t* off_
 extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_t precision,
                              uint32_t field_flags, void* ws, size_t* ws_bytes, lw_batch* plan,
                              void* stream) {
-    constexpr int PIX = 4;
+    constexpr int PIX = kMixPix;
     if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
     if (precision != LW_MIXED && precision != LW_MIXED_KAHAN) return LW_EUNSUPPORTED;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
@@ -802,7 +880,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
     plan->n_items = n_items;
     plan->n_units = (int32_t)sorted.size();
     plan->precision = precision;
-    plan->smem_bytes = (int32_t)(sizeof(float4) * max_block + sizeof(float) * 6 * (max_block + 1));
+    plan->smem_bytes = (int32_t)(2 * stage_bytes(max_block));
     plan->offsets[0] = (int64_t)o_counter;
     plan->offsets[1] = (int64_t)o_vars;
     plan->offsets[2] = (int64_t)o_units;
@@ -811,7 +889,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
 }
 
 extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
-    constexpr int PIX = 4;
+    constexpr int PIX = kMixPix;
     if (!plan || !plan->ws || plan->n_items < 1) return LW_EINVAL;
     cudaStream_t st = as_stream(stream);
     char* base = static_cast<char*>(plan->ws);

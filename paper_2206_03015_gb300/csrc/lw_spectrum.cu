@@ -14,9 +14,11 @@
 //               length N1 (coalesced column tiles) and applies the twiddles
 //               e^{2 pi i j2 l1 / N}, pass 2 transforms each row l1 together
 //               with its mirror row N1 - l1, which holds the Z_{N-l} needed by
-//               the split above.
+//               the split above, for the three sequences of a pixel pair at
+//               once, so each spectrum value is written exactly once.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "lw_fft.cuh"
@@ -124,11 +126,11 @@ __global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, in
 template <typename T, int CT>
 __global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N1, int logN1,
                                       int N2, T scale, const typename V2<T>::type* __restrict__ tw,
-                                      typename V2<T>::type* __restrict__ Y) {
+                                      typename V2<T>::type* __restrict__ Y, int64_t seq0) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);   // [N1][CT]
-    const int64_t seq = blockIdx.y;
+    const int64_t seq = seq0 + blockIdx.y;
     const int c0 = blockIdx.x * CT;
     const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
     for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
@@ -150,28 +152,32 @@ __global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int
     }
 }
 
-// Pass 2: rows l1 and N1 - l1 of sequence seq; transforms and emits spectra.
+// Pass 2: rows l1 and N1 - l1 of the three sequences of one pixel pair; transforms
+// them together and writes each spectrum value once (no atomics, no zeroing):
+// every l <= N/2 has row l mod N1, which one CTA holds as l1 or as its mirror.
 template <typename T>
 __global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2,
                                       const typename V2<T>::type* __restrict__ tw,
                                       const typename V2<T>::type* __restrict__ Y,
-                                      T* __restrict__ S, typename V2<T>::type* __restrict__ X) {
+                                      T* __restrict__ S, typename V2<T>::type* __restrict__ X,
+                                      int64_t pair0) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][2]
-    const int64_t seq = blockIdx.y;
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][kind * 2 + (row, mirror row)]
+    const int64_t pair = pair0 + blockIdx.y;
     const int l1 = blockIdx.x;                  // 0 .. N1/2
     const int l1p = (N1 - l1) & (N1 - 1);       // mirror row
-    const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
-    if (sr.ma < 0 && sr.mb < 0) return;
-    const C* Ys = Y + seq * (int64_t)N;
-    for (int t = threadIdx.x; t < 2 * N2; t += blockDim.x) {
-        const int c = t & 1, j2 = t >> 1;
+    const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
+    const bool has1 = m1 < n_pix;
+    for (int t = threadIdx.x; t < 6 * N2; t += blockDim.x) {
+        const int col = t % 6, j2 = t / 6;
+        const int kind = col >> 1, c = col & 1;
         const int row = c ? l1p : l1;
-        buf[bitrev(j2, logN2) * 2 + c] = Ys[(int64_t)row * N2 + j2];
+        const C* Ys = Y + (pair * 3 + kind) * (int64_t)N;
+        buf[bitrev(j2, logN2) * 6 + col] = Ys[(int64_t)row * N2 + j2];
     }
     __syncthreads();
-    fft_smem<C>(buf, N2, logN2, 2, tw, N);
+    fft_smem<C>(buf, N2, logN2, 6, tw, N);
     const int64_t nl = N / 2 + 1;
     const int64_t half = N / 2;
     for (int t = threadIdx.x; t < 2 * N2; t += blockDim.x) {
@@ -181,12 +187,42 @@ __global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int 
         const int64_t l = row + (int64_t)N1 * l2;
         if (l > half) continue;
         // mirror index N - l lives in the other column
-        int l2m;
-        if (row == 0) l2m = (N2 - l2) & (N2 - 1);
-        else l2m = N2 - 1 - l2;
-        const C zl = buf[l2 * 2 + c];
-        const C zn = buf[l2m * 2 + (1 - c)];
-        emit<T, C>(sr, l, zl, zn, nl, S, X, true);
+        const int l2m = row == 0 ? (N2 - l2) & (N2 - 1) : N2 - 1 - l2;
+        T pw0 = (T)0, pw1 = (T)0;
+#pragma unroll
+        for (int kind = 0; kind < 3; ++kind) {
+            const C zl = buf[l2 * 6 + kind * 2 + c];
+            const C zn = buf[l2m * 6 + kind * 2 + (1 - c)];
+            C A, B;   // spectra of the two real rows of the sequence
+            A.x = (T)0.5 * (zl.x + zn.x);
+            A.y = (T)0.5 * (zl.y - zn.y);
+            B.x = (T)0.5 * (zl.y + zn.y);
+            B.y = (T)0.5 * (zn.x - zl.x);
+            const T pa = A.x * A.x + A.y * A.y;
+            const T pb = B.x * B.x + B.y * B.y;
+            if (kind == 0) {          // (x0, y0)
+                pw0 += pa + pb;
+                if (X) {
+                    X[(m0 * 3 + 0) * nl + l] = A;
+                    X[(m0 * 3 + 1) * nl + l] = B;
+                }
+            } else if (kind == 1) {   // (x1, y1)
+                pw1 += pa + pb;
+                if (X && has1) {
+                    X[(m1 * 3 + 0) * nl + l] = A;
+                    X[(m1 * 3 + 1) * nl + l] = B;
+                }
+            } else {                  // (z0, z1)
+                pw0 += pa;
+                pw1 += pb;
+                if (X) {
+                    X[(m0 * 3 + 2) * nl + l] = A;
+                    if (has1) X[(m1 * 3 + 2) * nl + l] = B;
+                }
+            }
+        }
+        S[m0 * nl + l] = pw0;
+        if (has1) S[m1 * nl + l] = pw1;
     }
 }
 
@@ -198,6 +234,8 @@ template <> void set_reader<float>(RecReader<float>& rd, const void* rec, int ka
     rd.rec = rec;
     rd.kahan = kahan;
 }
+
+constexpr int64_t kPairsPerLaunch = 21845;   // 3 x pairs <= 65535 (grid y limit)
 
 template <typename T>
 int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g, double q,
@@ -235,9 +273,9 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     const int tw_grid = (int)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
     twiddle_kernel<T><<<tw_grid, 256, 0, st>>>(tw, N);
     if (launch_status() != LW_OK) return LW_ECUDA;
-    if (cudaMemsetAsync(S, 0, sizeof(T) * (size_t)nl * (size_t)n_pix, st) != cudaSuccess)
-        return LW_ECUDA;
     if (direct) {
+        if (cudaMemsetAsync(S, 0, sizeof(T) * (size_t)nl * (size_t)n_pix, st) != cudaSuccess)
+            return LW_ECUDA;
         const size_t smem = sizeof(C) * (size_t)N;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(spectrum_direct_kernel<T>,
@@ -258,17 +296,30 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return LW_ECUDA;
-        dim3 grid((unsigned)(N2 / CT), (unsigned)n_seq);
-        spectrum_pass1_kernel<T, CT><<<grid, 256, smem, st>>>(rd, n_pix, (int)N, N1, logN1, N2,
-                                                              scale, tw, Y);
-        if (launch_status() != LW_OK) return LW_ECUDA;
+        // grid y is limited to 65535: sequences in chunks of 21845 pixel pairs
+        for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
+            const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
+            dim3 grid((unsigned)(N2 / CT), (unsigned)(3 * np));
+            spectrum_pass1_kernel<T, CT><<<grid, 256, smem, st>>>(rd, n_pix, (int)N, N1, logN1,
+                                                                  N2, scale, tw, Y, 3 * p0);
+            if (launch_status() != LW_OK) return LW_ECUDA;
+        }
     }
     {
-        const size_t smem = sizeof(C) * (size_t)N2 * 2;
-        dim3 grid((unsigned)(N1 / 2 + 1), (unsigned)n_seq);
-        spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw, Y,
-                                                          S, X);
-        return launch_status();
+        const size_t smem = sizeof(C) * (size_t)N2 * 6;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(spectrum_pass2_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return LW_ECUDA;
+        for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
+            const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
+            dim3 grid((unsigned)(N1 / 2 + 1), (unsigned)np);
+            spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw,
+                                                              Y, S, X, p0);
+            if (launch_status() != LW_OK) return LW_ECUDA;
+        }
+        return LW_OK;
     }
 }
 

@@ -278,7 +278,7 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
     if (in->n_s >= (int64_t(1) << 30) || in->n_e >= (int64_t(1) << 31)) return LW_EUNSUPPORTED;
     if (!in->t || !in->r || !in->beta || !in->beta_dot) return LW_EINVAL;
     if (sections <= 0 || (sections & ~(LW_SECTION_FP64 | LW_SECTION_MIXED))) return LW_EINVAL;
-    if (block == 0) block = 128;
+    if (block == 0) block = 512;
     if (block < 16 || block > 1024 || (block & (block - 1))) return LW_EINVAL;
     const int t_per_e = in->t_per_electron ? 1 : 0;
     const TrajLayout L = make_layout(in->n_e, in->n_s, t_per_e, sections, block);

@@ -33,7 +33,7 @@ def grid_bounds_from_ends(t0, t1, r0, r1, det: "lw.Detector"):
 def in_situ_spectrum(r0, u0, laser, t_start: float, t_end: float, n_steps: int,
                      det: "lw.Detector", n_bins: int, precision: int = lw.LW_MIXED,
                      block_steps: int = 1024, grid: "lw.Grid | None" = None,
-                     q: float = lw.Q_E, anchor_block: int = 128):
+                     q: float = lw.Q_E, anchor_block: int = 512):
     """Spectra S [n_pix][n_bins/2+1] of electrons starting at (r0, u0) ([n_e, 3] float64 CUDA
     tensors; u = gamma beta) in the Gaussian laser (lam, a0, w0, fwhm).  Without ``grid`` the
     observer grid comes from a trial push (Eqs. tu_min / tu_max of the first and last

@@ -240,7 +240,7 @@ def _as_input(x, device):
 
 
 def lw_trajectories_upload(t, r, beta, beta_dot, sections=LW_SECTION_FP64 | LW_SECTION_MIXED,
-                           block: int = 128, device="cuda", ws=None) -> Trajectories:
+                           block: int = 512, device="cuda", ws=None) -> Trajectories:
     """Copy trajectories (t, r, beta, beta_dot; CUDA or pinned-CPU float64 tensors,
     or numpy arrays) into the device layout (see lw.h).  ``ws`` may pass a
     previously returned workspace (``Trajectories.ws``) for reuse."""
