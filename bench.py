@@ -344,10 +344,11 @@ def run_ours(args, rank, world, dist):
                          "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": S_host.numel() * S_host.element_size(),
                          "ms_per_step": ms_e / args.steps}
-    # launches of our kernels per step: upload (ends, check, build), deposit (1),
-    # spectrum (twiddle, pass1, pass2 | direct)
+    # launches of our kernels per timed step: upload (ends, prepare, and the electron
+    # order: key init, range, count, scan, scatter), deposit (1), spectrum (twiddle, then
+    # pass 1 + pass 2, or the direct kernel up to 4096 bins)
     spec_k = 2 if grid.n_bins <= 4096 else 3
-    result["gpu_launches"] = args.steps * (3 + 1 + spec_k)
+    result["gpu_launches"] = args.steps * (7 + 1 + spec_k)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, grid, S_m, args)
     return result

@@ -66,28 +66,44 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
     return L;
 }
 
-// One pass over the samples (grid: x = samples of an electron, y = electrons):
-// input checks of every sample -- finite values, |beta| < 1 (evaluated as
-// ((bx*bx + by*by) + bz*bz) < 1), strictly increasing lab time -- and, when
-// `scan` is non-null, the mixed section (block-relative float4, six field
-// floats, per-block FP64 anchor).  Reading each sample once serves both.
-__global__ void prepare_kernel(const double* __restrict__ t, int t_per_e,
-                               const double* __restrict__ r, const double* __restrict__ beta,
-                               const double* __restrict__ bdot, int64_t n_e, int ns1,
-                               int block_shift, int n_blocks, float4* __restrict__ scan,
-                               float* __restrict__ field, D4* __restrict__ anchor,
-                               int32_t* __restrict__ status) {
+// One pass over the samples (CTA = 256 consecutive samples of one electron;
+// grid x = sample chunks, y = electrons): input checks of every sample --
+// finite values, |beta| < 1 (evaluated as ((bx*bx + by*by) + bz*bz) < 1),
+// strictly increasing lab time -- and, when `scan` is non-null, the mixed
+// section (block-relative float4, six field floats, per-block FP64 anchor).
+// The [sample][3] inputs and the [sample][6] field output are moved through
+// shared memory so that every global access is a contiguous run.
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads)
+    prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
+                   const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
+                   int ns1, int block_shift, int n_blocks, float4* __restrict__ scan,
+                   float* __restrict__ field, D4* __restrict__ anchor,
+                   int32_t* __restrict__ status) {
+    __shared__ double s_in[3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
+    __shared__ float s_out[6 * kPrepThreads];       // field records of the chunk
     int bits = 0;
+    const int i_first = blockIdx.x * kPrepThreads;
+    const int cnt = min(kPrepThreads, ns1 - i_first);
     for (int64_t k = blockIdx.y; k < n_e; k += gridDim.y) {
+        const int64_t s0 = k * ns1 + i_first;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 3 * cnt; q += kPrepThreads) {
+            s_in[0][q] = r[3 * s0 + q];
+            s_in[1][q] = beta[3 * s0 + q];
+            s_in[2][q] = bdot[3 * s0 + q];
+        }
+        __syncthreads();
         const double* tk = t + (t_per_e ? k * ns1 : 0);
         const bool check_t = t_per_e || k == 0;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns1; i += gridDim.x * blockDim.x) {
-            const int64_t s = k * ns1 + i;
-            const double x = r[3 * s], y = r[3 * s + 1], z = r[3 * s + 2];
-            const double* b = beta + 3 * s;
-            const double* a = bdot + 3 * s;
-            const double b0 = b[0], b1 = b[1], b2 = b[2];
-            const double a0 = a[0], a1 = a[1], a2 = a[2];
+        const int l = threadIdx.x;
+        if (l < cnt) {
+            const int i = i_first + l;
+            const int64_t s = s0 + l;
+            const double x = s_in[0][3 * l], y = s_in[0][3 * l + 1], z = s_in[0][3 * l + 2];
+            const double b0 = s_in[1][3 * l], b1 = s_in[1][3 * l + 1], b2 = s_in[1][3 * l + 2];
+            const double a0 = s_in[2][3 * l], a1 = s_in[2][3 * l + 1], a2 = s_in[2][3 * l + 2];
             const double ti = tk[i];
             const bool fin = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(b0) &&
                              isfinite(b1) && isfinite(b2) && isfinite(a0) && isfinite(a1) &&
@@ -105,15 +121,18 @@ __global__ void prepare_kernel(const double* __restrict__ t, int t_per_e,
                 const double taub = tk[ib] - zb * kInvC0;
                 scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
                                       (float)(z - zb));
-                float* f = field + 6 * s;
-                f[0] = (float)b0;
-                f[1] = (float)b1;
-                f[2] = (float)(1.0 - b2);
-                f[3] = (float)a0;
-                f[4] = (float)a1;
-                f[5] = (float)a2;
+                s_out[6 * l] = (float)b0;
+                s_out[6 * l + 1] = (float)b1;
+                s_out[6 * l + 2] = (float)(1.0 - b2);
+                s_out[6 * l + 3] = (float)a0;
+                s_out[6 * l + 4] = (float)a1;
+                s_out[6 * l + 5] = (float)a2;
                 if (i == ib) anchor[k * n_blocks + (i >> block_shift)] = D4{taub, xb, yb, zb};
             }
+        }
+        if (scan) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < 6 * cnt; q += kPrepThreads) field[6 * s0 + q] = s_out[q];
         }
     }
     block_status_or(status, bits);
@@ -347,9 +366,9 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
     }
     int shift = 0;
     while ((1 << shift) < block) ++shift;
-    const dim3 g((unsigned)std::min<int64_t>((ns1 + threads - 1) / threads, 1024),
+    const dim3 g((unsigned)((ns1 + kPrepThreads - 1) / kPrepThreads),
                  (unsigned)std::min<int64_t>(in->n_e, 65535));
-    prepare_kernel<<<g, threads, 0, st>>>(t, t_per_e, r, beta, bdot, in->n_e, (int)ns1, shift,
+    prepare_kernel<<<g, kPrepThreads, 0, st>>>(t, t_per_e, r, beta, bdot, in->n_e, (int)ns1, shift,
                                           L.n_blocks, scan, field, anchor, status);
     if (launch_status() != LW_OK) return LW_ECUDA;
     if (sections & LW_SECTION_MIXED) {
