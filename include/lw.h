@@ -290,7 +290,9 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
  * and record) deposited by one persistent launch of the mixed-precision
  * deposit (LW_MIXED or LW_MIXED_KAHAN).  The work is cut into units of
  * (variant, 512-pixel tile, chunk of electrons) that resident CTAs take from a
- * list, largest first, so variants of very different sizes share the GPU.
+ * list: variants largest first, each variant's chunks in arrival order (the
+ * upload's electron order) with its tiles fastest, so variants of very
+ * different sizes share the GPU and each keeps its record updates local.
  * Two calls:
  *   lw_batch_plan     checks the items, writes the per-variant arguments and the
  *                     work list into `ws` (NULL = size query) and fills `plan`;

@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
         __syncthreads();
         if (u >= n_units) break;
         const BatchUnit un = units[u];
-        const DepositArgs p = vars[un.variant];
+        const DepositArgs& p = vars[un.variant];
         const int bits = mixed_cta<PIX, KAHAN>(p, un.tile, un.chunk);
         block_status_or(p.status, bits);
     }
@@ -850,10 +850,20 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
             }
     }
     // largest units first
+    // variants largest first (their total work), each variant's units in their own
+    // order (electron chunks in arrival order, tiles fastest), so that the units in
+    // flight keep the record band of one variant narrow
+    std::vector<int64_t> var_work((size_t)n_items, 0);
+    for (size_t i = 0; i < units.size(); ++i) var_work[(size_t)units[i].variant] += unit_work[i];
     std::vector<size_t> order(units.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t x, size_t y) { return unit_work[x] > unit_work[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const int vx = units[x].variant, vy = units[y].variant;
+        if (vx == vy) return false;
+        if (var_work[(size_t)vx] != var_work[(size_t)vy])
+            return var_work[(size_t)vx] > var_work[(size_t)vy];
+        return vx < vy;
+    });
     std::vector<BatchUnit> sorted(units.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
     size_t o_vars, o_units, o_counter;

@@ -75,6 +75,11 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
 // shared memory so that every global access is a contiguous run.
 constexpr int kPrepThreads = 256;
 
+// isfinite on the exponent bits (integer pipe; the FP64 pipe is the upload's bound)
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((__double2hiint(v) >> 20) & 0x7ff) != 0x7ff;
+}
+
 __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
@@ -105,13 +110,22 @@ __global__ void __launch_bounds__(kPrepThreads)
             const double b0 = s_in[1][3 * l], b1 = s_in[1][3 * l + 1], b2 = s_in[1][3 * l + 2];
             const double a0 = s_in[2][3 * l], a1 = s_in[2][3 * l + 1], a2 = s_in[2][3 * l + 2];
             const double ti = tk[i];
-            const bool fin = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(b0) &&
-                             isfinite(b1) && isfinite(b2) && isfinite(a0) && isfinite(a1) &&
-                             isfinite(a2) && isfinite(ti);
+            const bool fin = finite_bits(x) & finite_bits(y) & finite_bits(z) &
+                             finite_bits(b0) & finite_bits(b1) & finite_bits(b2) &
+                             finite_bits(a0) & finite_bits(a1) & finite_bits(a2) &
+                             finite_bits(ti);
             if (!fin) bits |= LW_ST_NONFINITE;
-            const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
-                                        __dmul_rn(b2, b2));
-            if (!(bb < 1.0)) bits |= LW_ST_BETA;
+            // |beta| < 1: decided in FP32 when 1 - beta^2 is far above its FP32 rounding,
+            // else by the FP64 expression ((bx*bx + by*by) + bz*bz) < 1
+            const float b0f = (float)b0, b1f = (float)b1;
+            const float epsf = (float)(1.0 - b2);   // exact in FP64 for b2 in [0.5, 2]
+            const float perp = fmaf(b0f, b0f, b1f * b1f);
+            const float one_minus = fmaf(-epsf, epsf, 2.0f * epsf) - perp;   // 1 - beta^2
+            if (!(b2 >= 0.5 && one_minus > 1.0e-5f * (2.0f * epsf + perp))) {
+                const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
+                                            __dmul_rn(b2, b2));
+                if (!(bb < 1.0)) bits |= LW_ST_BETA;
+            }
             if (check_t && i > 0 && !(ti > tk[i - 1])) bits |= LW_ST_TIME;
             if (scan) {
                 const int ib = (i >> block_shift) << block_shift;
@@ -121,9 +135,9 @@ __global__ void __launch_bounds__(kPrepThreads)
                 const double taub = tk[ib] - zb * kInvC0;
                 scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
                                       (float)(z - zb));
-                s_out[6 * l] = (float)b0;
-                s_out[6 * l + 1] = (float)b1;
-                s_out[6 * l + 2] = (float)(1.0 - b2);
+                s_out[6 * l] = b0f;
+                s_out[6 * l + 1] = b1f;
+                s_out[6 * l + 2] = epsf;
                 s_out[6 * l + 3] = (float)a0;
                 s_out[6 * l + 4] = (float)a1;
                 s_out[6 * l + 5] = (float)a2;
