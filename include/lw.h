@@ -303,7 +303,8 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
  * e_chunk (electrons per unit) comes from the item, or is chosen so that the
  * batch splits into about eight units per resident CTA when it is 0.  Records
  * and results are those of lw_deposit_time_domain for each variant.
- * Errors: LW_EINVAL, LW_EUNSUPPORTED (LW_FP64), LW_ESIZE, LW_ECUDA. */
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (LW_FP64, or more than 65,535 items), LW_ESIZE,
+ * LW_ECUDA. */
 typedef struct {
     const lw_traj* traj;        /* uploaded with the mixed section */
     const lw_detector* det;

@@ -648,26 +648,35 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     deposit_batched_kernel(const DepositArgs* __restrict__ vars,
                            const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
+    __shared__ DepositArgs s_p;   // the unit's variant arguments, read by every thread
     while (true) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
         __syncthreads();
         const int u = s_unit;
-        __syncthreads();
         if (u >= n_units) break;
         const BatchUnit un = units[u];
-        const DepositArgs& p = vars[un.variant];
-        const int bits = mixed_cta<PIX, KAHAN>(p, un.tile, un.chunk);
-        block_status_or(p.status, bits);
+        if (threadIdx.x == 0) s_p = vars[un.variant];
+        __syncthreads();
+        const int bits = mixed_cta<PIX, KAHAN>(s_p, un.tile, un.chunk);
+        block_status_or(s_p.status, bits);
     }
 }
 
-__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int n_vars) {
-    for (int v = 0; v < n_vars; ++v) {
-        double* rec = static_cast<double*>(vars[v].record);   // 8-byte values in every precision
-        const int64_t n = vars[v].n_pix * 3 * vars[v].n_bins;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x)
-            rec[i] = 0.0;
+// Zeroes every variant's record (n_pix * 3 * n_bins values of 8 bytes): grid y =
+// variant, x = CTAs striding over it, with 16-byte stores where the record is
+// 16-byte aligned (an odd last value is stored alone).
+__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars) {
+    const DepositArgs& a = vars[blockIdx.y];
+    const int64_t n = a.n_pix * 3 * a.n_bins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(a.record) & 15) == 0) {
+        float4* rec = static_cast<float4*>(a.record);
+        for (int64_t i = i0; i < n / 2; i += stride) rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((n & 1) && i0 == 0) static_cast<double*>(a.record)[n - 1] = 0.0;
+    } else {
+        double* rec = static_cast<double*>(a.record);
+        for (int64_t i = i0; i < n; i += stride) rec[i] = 0.0;
     }
 }
 
@@ -786,6 +795,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
                              void* stream) {
     constexpr int PIX = kMixPix;
     if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
+    if (n_items > 65535) return LW_EUNSUPPORTED;
     if (precision != LW_MIXED && precision != LW_MIXED_KAHAN) return LW_EUNSUPPORTED;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     std::vector<DepositArgs> vars((size_t)n_items);
@@ -906,7 +916,7 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     int* counter = reinterpret_cast<int*>(base + plan->offsets[0]);
     const DepositArgs* vars = reinterpret_cast<const DepositArgs*>(base + plan->offsets[1]);
     const BatchUnit* units = reinterpret_cast<const BatchUnit*>(base + plan->offsets[2]);
-    zero_records_kernel<<<kSms * 8, 256, 0, st>>>(vars, plan->n_items);
+    zero_records_kernel<<<dim3(kSms * 4, (unsigned)plan->n_items), 256, 0, st>>>(vars);
     if (launch_status() != LW_OK) return LW_ECUDA;
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return LW_ECUDA;
     auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, true>

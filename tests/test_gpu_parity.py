@@ -168,3 +168,25 @@ def test_upload_orders_electrons_by_first_light_front_time():
     assert np.mean(np.diff(bucket[order]) >= 0) > 0.99
     assert lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
                                       sections=lw.LW_SECTION_FP64).order() is None
+
+
+@pytest.mark.parametrize("precision", [lw.LW_FP64, lw.LW_MIXED])
+def test_electron_chunks_accumulate_to_the_whole_deposit(precision):
+    """The record is a sum over electrons: depositing electron chunks from pinned host
+    inputs into one record (accumulate) equals one deposit of all electrons from
+    device inputs, up to the order of the FP64 additions."""
+    tr, n_hat, grid, flags, R = _case("c1_offsets")
+    det = lw.Detector(n_hat)
+    whole = lw.lw_deposit_time_domain(lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot),
+                                      det, grid, precision)
+    h = [torch.from_numpy(x).pin_memory() for x in (tr.t, tr.r, tr.beta, tr.beta_dot)]
+    shp, dt = lw.record_shape(det, grid, precision)
+    rec = torch.zeros(shp, dtype=dt, device="cuda")
+    cuts = [0, 3, 4, 11, tr.n_e]
+    for k0, k1 in zip(cuts[:-1], cuts[1:]):
+        part = lw.lw_trajectories_upload(h[0], h[1][k0:k1], h[2][k0:k1], h[3][k0:k1])
+        lw.lw_deposit_time_domain(part, det, grid, precision, record=rec, accumulate=True)
+    torch.cuda.synchronize()
+    a = lw.record_value(rec, precision).cpu().numpy()
+    b = lw.record_value(whole, precision).cpu().numpy()
+    assert rel_l2(a, b) <= 1e-12   # the same per-electron contributions, summed in FP64
