@@ -277,55 +277,6 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     st_m = int(status.item())
 
-    # FP64 path beside it (fewer steps: it is ~two orders slower on GB300's FP64 pipe)
-    fp64 = None
-    S_64 = None
-    if not args.no_fp64:
-        del traj0
-        rec_d = torch.empty(lw.record_shape(det, grid, lw.LW_FP64)[0], dtype=torch.float64,
-                            device=dev)
-        S_d = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float64, device=dev)
-        ws_sd = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_FP64, det.n_pix, grid), dev)
-        trajd = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
-                                          device=dev)
-        ws_d = trajd.ws
-
-        def step_fp64(timed=False):
-            tj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
-                                           device=dev, ws=ws_d)
-            lw.lw_deposit_time_domain(tj, det, grid, lw.LW_FP64, record=rec_d, status=status)
-            lw.lw_spectrum(rec_d, lw.LW_FP64, det.n_pix, grid, ws=ws_sd, out=S_d)
-
-        k64 = max(1, min(args.steps, args.fp64_steps))
-        ms_d, _ = timed_loop(step_fp64, k64, 1)
-        fp64 = {"value": n_dep * world / (ms_d / k64 * 1e-3), "ms_per_step": ms_d / k64,
-                "steps": k64, "warmup": 1}
-        S_64 = S_d
-    # accuracy of the mixed spectrum against the FP64 GPU spectrum (parity-tested vs oracle)
-    acc = {}
-    if S_64 is not None:
-        a = S_m.double()
-        b = S_64
-        acc["spectrum_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(a - b) /
-                                                     torch.linalg.norm(b))
-        # per band, on-axis-like fundamental omega_1(theta) +-20% and its 2nd harmonic
-        from workloads.planewave import doppler_fundamental
-        om = grid.omega.to(dev)
-        th2 = torch.from_numpy(w.theta_x**2 + w.theta_y**2).to(dev)
-        w1 = doppler_fundamental(w.gamma, w.lam, w.a0) / (1.0 + (w.gamma**2) * th2 /
-                                                          (1 + 0.5 * w.a0**2))
-        for name, h in (("fundamental", 1.0), ("harmonic2", 2.0)):
-            mask = (om[None, :] > 0.8 * h * w1[:, None]) & (om[None, :] < 1.2 * h * w1[:, None])
-            if bool(mask.any()):
-                acc[f"rel_l2_{name}"] = float(torch.linalg.norm((a - b)[mask]) /
-                                              torch.linalg.norm(b[mask]))
-            else:
-                acc[f"rel_l2_{name}"] = None
-                acc[f"{name}_note"] = "band above Nyquist of this grid (aliased record)"
-    result["fp64"] = fp64
-    result["accuracy"] = acc
-    result["status"] = {"mixed": st_m, "note": "8 = last arrival on grid point n_bins (clipped)"}
-
     # end to end through the C ABI from pinned host buffers, spectrum read back: the
     # electrons are streamed in chunks -- the upload of chunk c+1 (DMA of its FP64 inputs
     # into the workspace's FP64 section, then the relayout) runs on one stream while
@@ -379,6 +330,57 @@ def run_ours(args, rank, world, dist):
                          "d2h_bytes_per_step": S_host.numel() * S_host.element_size(),
                          "ms_per_step": ms_e / args.steps,
                          "pipeline": f"{n_ch} electron chunks, upload and deposit streams"}
+        del ws_up, h
+    # FP64 path beside it (fewer steps: GB300's FP64 pipe is 1/70 of its FP32 rate); timed
+    # after the end-to-end steps, whose timing its memory use was seen to disturb
+    fp64 = None
+    S_64 = None
+    if not args.no_fp64:
+        del traj0
+        rec_d = torch.empty(lw.record_shape(det, grid, lw.LW_FP64)[0], dtype=torch.float64,
+                            device=dev)
+        S_d = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float64, device=dev)
+        ws_sd = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_FP64, det.n_pix, grid), dev)
+        trajd = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
+                                          device=dev)
+        ws_d = trajd.ws
+
+        def step_fp64(timed=False):
+            tj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_FP64,
+                                           device=dev, ws=ws_d)
+            lw.lw_deposit_time_domain(tj, det, grid, lw.LW_FP64, record=rec_d, status=status)
+            lw.lw_spectrum(rec_d, lw.LW_FP64, det.n_pix, grid, ws=ws_sd, out=S_d)
+
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        ms_d, _ = timed_loop(step_fp64, k64, 1)
+        fp64 = {"value": n_dep * world / (ms_d / k64 * 1e-3), "ms_per_step": ms_d / k64,
+                "steps": k64, "warmup": 1}
+        S_64 = S_d
+    # accuracy of the mixed spectrum against the FP64 GPU spectrum (parity-tested vs oracle)
+    acc = {}
+    if S_64 is not None:
+        a = S_m.double()
+        b = S_64
+        acc["spectrum_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(a - b) /
+                                                     torch.linalg.norm(b))
+        # per band, on-axis-like fundamental omega_1(theta) +-20% and its 2nd harmonic
+        from workloads.planewave import doppler_fundamental
+        om = grid.omega.to(dev)
+        th2 = torch.from_numpy(w.theta_x**2 + w.theta_y**2).to(dev)
+        w1 = doppler_fundamental(w.gamma, w.lam, w.a0) / (1.0 + (w.gamma**2) * th2 /
+                                                          (1 + 0.5 * w.a0**2))
+        for name, h in (("fundamental", 1.0), ("harmonic2", 2.0)):
+            mask = (om[None, :] > 0.8 * h * w1[:, None]) & (om[None, :] < 1.2 * h * w1[:, None])
+            if bool(mask.any()):
+                acc[f"rel_l2_{name}"] = float(torch.linalg.norm((a - b)[mask]) /
+                                              torch.linalg.norm(b[mask]))
+            else:
+                acc[f"rel_l2_{name}"] = None
+                acc[f"{name}_note"] = "band above Nyquist of this grid (aliased record)"
+    result["fp64"] = fp64
+    result["accuracy"] = acc
+    result["status"] = {"mixed": st_m, "note": "8 = last arrival on grid point n_bins (clipped)"}
+
     # launches of our kernels per timed step: upload (ends, prepare, and the electron
     # order: key init, range, count, scan, scatter), deposit (1), spectrum (twiddle, then
     # pass 1 + pass 2, or the direct kernel up to 4096 bins)

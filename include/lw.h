@@ -77,7 +77,10 @@ enum {
     LW_ST_NONFINITE = 2,   /* non-finite input, or a bin coordinate beyond +-2^62 */
     LW_ST_TIME = 4,        /* lab time not strictly increasing along a trajectory */
     LW_ST_CLIP = 8,        /* grid points outside [0, n_bins) were skipped */
-    LW_ST_TA_ORDER = 16    /* advanced time not increasing between two samples (LW_FP64) */
+    LW_ST_TA_ORDER = 16,   /* advanced time not increasing between two samples (LW_FP64) */
+    LW_ST_STEP = 32        /* two consecutive samples at least c0 (t_i - t_(i-1)) apart
+                              (checked by uploads with the FP64 section): the advanced time
+                              may decrease for some direction */
 };
 
 /* Which device sections lw_trajectories_upload builds (bit mask). */
@@ -121,10 +124,10 @@ typedef struct {
     const double* ends;     /* always: double [n_e][2][4] = (t, x, y, z) of the first and
                                the last sample of each electron */
     const int32_t* input_status; /* device int32: LW_ST_* found while uploading */
-    const int32_t* order;   /* MIXED: int32 [n_e] electron indices in increasing light-front
+    const int32_t* order;   /* always: int32 [n_e] electron indices in increasing light-front
                                time tau = t - z/c0 of the first sample (bucketed: the order
-                               within 1/4096 of the range is unspecified); the mixed
-                               deposit visits electrons in this order */
+                               within 1/4096 of the range is unspecified); the deposits
+                               visit electrons in this order */
 } lw_traj;
 
 /* Far-field detector: n_pix unit directions n_hat [n_pix][3] (float64, device) on a
@@ -300,10 +303,14 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
  *   lw_batch_deposit  zeroes every record and launches the persistent kernel;
  *                     it only enqueues stream-ordered work, so it can be
  *                     repeated (and recorded in a CUDA graph) with the same plan.
+ *                     The variants' arguments are copied into a constant-memory
+ *                     table of the library before the launch: calls of
+ *                     lw_batch_deposit must not overlap on the GPU (serialise them
+ *                     on one stream).
  * e_chunk (electrons per unit) comes from the item, or is chosen so that the
  * batch splits into about eight units per resident CTA when it is 0.  Records
  * and results are those of lw_deposit_time_domain for each variant.
- * Errors: LW_EINVAL, LW_EUNSUPPORTED (LW_FP64, or more than 65,535 items), LW_ESIZE,
+ * Errors: LW_EINVAL, LW_EUNSUPPORTED (LW_FP64, or more than 256 items), LW_ESIZE,
  * LW_ECUDA. */
 typedef struct {
     const lw_traj* traj;        /* uploaded with the mixed section */

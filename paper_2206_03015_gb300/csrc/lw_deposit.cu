@@ -103,7 +103,9 @@ __device__ int field_fp64(double nx, double ny, double nz, double R, uint32_t fl
     return 0;
 }
 
-__global__ void __launch_bounds__(kFp64Threads) deposit_fp64_kernel(DepositArgs p) {
+// Algorithm 2 literally: every step of every (pixel, electron), in the oracle's
+// operation order (CTA = kFp64Threads pixels x p.e_chunk electrons).
+__device__ void fp64_scan_cta(const DepositArgs& p) {
     __shared__ double s_t[kFp64Tile];
     __shared__ double s_r[kFp64Tile * 3];
     const int64_t m = (int64_t)blockIdx.x * kFp64Threads + threadIdx.x;
@@ -339,7 +341,7 @@ __host__ __device__ constexpr size_t stage_bytes(int B) {
 // fields and adding the interpolated value.  Blocks are staged into two
 // alternating shared buffers by asynchronous copies, one block ahead.
 template <int PIX, bool KAHAN>
-__device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
+__device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     constexpr int kSlots = kMixThreads * PIX;
     const int B = p.block;
@@ -628,6 +630,212 @@ __device__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     return bits;
 }
 
+// FP64 deposit for trajectories whose advanced time increases (no LW_ST_STEP
+// from the upload): per pixel and block of samples, the grid points reached
+// are the run (floor(u_b), floor(u_end)]; each is located, by a bracketed
+// search over the staged block, at the first sample whose coordinate reaches
+// it -- the step of Algorithm 2 that holds it -- and deposited with the scan's
+// FP64 expressions in the oracle's operation order, so every contribution is
+// bit-identical to the literal scan (only the order of the atomic additions
+// differs).  With LW_ST_STEP set the literal scan runs instead.
+constexpr int kF64Block = 256;   // samples staged per block
+
+__global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(DepositArgs p) {
+    if (p.input_status && (*p.input_status & LW_ST_STEP)) {
+        fp64_scan_cta(p);
+        return;
+    }
+    constexpr int kWarpsF = kFp64Threads / 32;
+    __shared__ double s_t[2][kF64Block + 1];        // sample i0-1 first
+    __shared__ double s_r[2][3 * (kF64Block + 1)];
+    __shared__ double s_n[kFp64Threads][3];         // pixel directions
+    __shared__ double s_ua[kFp64Threads];           // block: coordinate before the block
+    __shared__ double s_ue[kFp64Threads];           // block: coordinate of its last sample
+    __shared__ int s_ja[kFp64Threads];              // block: first grid point of the run
+    __shared__ int s_kp[kFp64Threads];              // block: job offset in the warp
+    __shared__ int2 s_tab[kWarpsF][kJobTable];      // block: (slot, grid point) of job t
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wslot = warp * 32;
+    const int64_t pix0 = (int64_t)blockIdx.x * kFp64Threads;
+    const int64_t m = pix0 + threadIdx.x;
+    const bool active = m < p.n_pix;
+    const int nb = (int)p.n_bins;
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    if (active) {
+        nx = p.n_hat[3 * m];
+        ny = p.n_hat[3 * m + 1];
+        nz = p.n_hat[3 * m + 2];
+    }
+    s_n[threadIdx.x][0] = nx;
+    s_n[threadIdx.x][1] = ny;
+    s_n[threadIdx.x][2] = nz;
+    int bits = 0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.input_status)
+        bits |= *p.input_status;
+    const int nblk = (int)((p.ns1 + kF64Block - 1) / kF64Block);
+    auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
+    auto issue = [&](int64_t k, int b, int buf) {
+        const int64_t i0 = (int64_t)b * kF64Block;
+        const int n = (int)min((int64_t)kF64Block, p.ns1 - i0);
+        const double* tk = p.t + (p.t_per_e ? k * p.ns1 : 0) + i0;
+        const double* rk = p.r + 3 * (k * p.ns1 + i0);
+        for (int q = (b == 0 ? 1 : 0) + threadIdx.x; q <= n; q += kFp64Threads)
+            cp_async8(&s_t[buf][q], tk + (q - 1));
+        for (int q = (b == 0 ? 3 : 0) + threadIdx.x; q < 3 * (n + 1); q += kFp64Threads)
+            cp_async8(&s_r[buf][q], rk + (q - 3));
+        cp_async_commit();
+    };
+    // coordinate u = (t_a - t_min) / dt_u of staged sample q, the scan's expression
+    auto coord64 = [&](const double* n3, int buf, int q) -> double {
+        const double ta = advanced_time_fp64(n3[0], n3[1], n3[2], s_r[buf][3 * q],
+                                             s_r[buf][3 * q + 1], s_r[buf][3 * q + 2],
+                                             s_t[buf][q]);
+        return __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
+    };
+    const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
+    const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
+    int buf = 0;
+    if (k0 < k1) issue(electron(k0), 0, 0);
+    for (int64_t kk = k0; kk < k1; ++kk) {
+        const int64_t k = electron(kk);
+        const double* bk = p.beta + 3 * k * p.ns1;
+        const double* ak = p.bdot + 3 * k * p.ns1;
+        const double* e0 = p.ends + 8 * k;
+        const double u0 = __dmul_rn(__dsub_rn(advanced_time_fp64(nx, ny, nz, e0[1], e0[2], e0[3],
+                                                                 e0[0]),
+                                              p.t_min),
+                                    p.inv_dtu);
+        bool ok = fabs(u0) < 4.0e18;
+        if (active && !ok) bits |= LW_ST_NONFINITE;
+        int64_t jdone = ok ? (int64_t)floor(u0) : 0;
+        double uprev = u0;
+        for (int b = 0; b < nblk; ++b) {
+            const int64_t i0 = (int64_t)b * kF64Block;
+            const int n = (int)min((int64_t)kF64Block, p.ns1 - i0);
+            cp_async_wait_all();
+            __syncthreads();   // block b staged; every warp is done with block b-1
+            if (b + 1 < nblk)
+                issue(k, b + 1, buf ^ 1);
+            else if (kk + 1 < k1)
+                issue(electron(kk + 1), 0, buf ^ 1);
+            const int cb = buf;
+            buf ^= 1;
+            const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
+            const double ue = coord64(s_n[threadIdx.x], cb, n);
+            int K = 0, ja = 0, big = 0;
+            if (active && ok && n > lo0) {
+                if (!(fabs(ue) < 4.0e18)) {
+                    bits |= LW_ST_NONFINITE;
+                    ok = false;
+                } else {
+                    const int64_t jend = (int64_t)floor(ue);
+                    int64_t a = jdone + 1, z = jend;
+                    if (a <= z) {
+                        if (a < 0) {
+                            a = 0;
+                            bits |= LW_ST_CLIP;
+                        }
+                        if (z > nb - 1) {
+                            z = nb - 1;
+                            bits |= LW_ST_CLIP;
+                        }
+                        if (a <= z) {
+                            K = (int)(z - a + 1);
+                            ja = (int)a;
+                            if (K > kMaxWarpJobs) {
+                                big = K;
+                                K = 0;
+                            }
+                        }
+                    }
+                    if (jend > jdone) jdone = jend;
+                }
+            }
+            s_ja[threadIdx.x] = ja;
+            s_ua[threadIdx.x] = b == 0 ? u0 : uprev;
+            s_ue[threadIdx.x] = ue;
+            uprev = ue;
+            // the warp's grid points: prefix sum, the first kJobTable listed by owners
+            int incl = K;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const int T = __shfl_sync(0xffffffffu, incl, 31);
+            const int run = incl - K;
+            s_kp[threadIdx.x] = run;
+            for (int t = 0; t < K && run + t < kJobTable; ++t)
+                s_tab[warp][run + t] = make_int2(threadIdx.x, ja + t);
+            __syncwarp();
+            // grid point j of slot sl: locate its step in the staged block and deposit
+            auto job = [&](int sl, int j) {
+                const double* n3 = s_n[sl];
+                const double J = (double)j;
+                // first staged sample in [lo0, n-1] (local index) with u >= j
+                int a = lo0 - 1, hb = n - 1;
+                double xa = s_ua[sl], xb = s_ue[sl];
+                bool interp = true;
+                while (hb - a > 1) {
+                    int g = (a + hb) >> 1;
+                    if (interp) {
+                        const float fr = __fdividef((float)(J - xa), (float)(xb - xa));
+                        const float gf = ceilf(fr * (float)(hb - a));
+                        g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
+                    }
+                    interp = !interp;
+                    const double xg = coord64(n3, cb, g + 1);
+                    if (xg >= J) {
+                        hb = g;
+                        xb = xg;
+                    } else {
+                        a = g;
+                        xa = xg;
+                    }
+                }
+                const int i = hb;   // local index of the step's end sample
+                const int q = i + 1;
+                const double ta = advanced_time_fp64(n3[0], n3[1], n3[2], s_r[cb][3 * q],
+                                                     s_r[cb][3 * q + 1], s_r[cb][3 * q + 2],
+                                                     s_t[cb][q]);
+                const double tb = advanced_time_fp64(n3[0], n3[1], n3[2], s_r[cb][3 * q - 3],
+                                                     s_r[cb][3 * q - 2], s_r[cb][3 * q - 1],
+                                                     s_t[cb][q - 1]);
+                const int64_t gi = i0 + i;   // global sample index of the step's end
+                double Fb[3], Fa[3];
+                field_fp64(n3[0], n3[1], n3[2], p.R, p.flags, bk + 3 * (gi - 1), ak + 3 * (gi - 1),
+                           Fb);
+                field_fp64(n3[0], n3[1], n3[2], p.R, p.flags, bk + 3 * gi, ak + 3 * gi, Fa);
+                const double den = __dsub_rn(ta, tb);
+                const double tu = __dadd_rn(p.t_min, __dmul_rn(J, p.dt_u));
+                const double wa = __ddiv_rn(__dsub_rn(ta, tu), den);
+                const double wb = __ddiv_rn(__dsub_rn(tu, tb), den);
+                double* rec = static_cast<double*>(p.record) + (pix0 + sl) * 3 * p.n_bins + j;
+                for (int c = 0; c < 3; ++c)
+                    atomicAdd(rec + c * p.n_bins,
+                              __dadd_rn(__dmul_rn(Fb[c], wa), __dmul_rn(Fa[c], wb)));
+            };
+            for (int t = lane; t < T; t += 32) {
+                if (t < kJobTable) {
+                    const int2 e = s_tab[warp][t];
+                    job(e.x, e.y);
+                } else {
+                    int pos = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (s_kp[wslot + pos + step] <= t) pos += step;
+                    const int sl = wslot + pos;
+                    job(sl, s_ja[sl] + (t - s_kp[sl]));
+                }
+            }
+            for (int t = 0; t < big; ++t) job(threadIdx.x, ja + t);   // runs beyond the warp count
+            __syncwarp();
+        }
+    }
+    cp_async_wait_all();
+    block_status_or(p.status, bits);
+}
+
 template <int PIX, bool KAHAN>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
     const int bits = mixed_cta<PIX, KAHAN>(p, blockIdx.x, blockIdx.y);
@@ -643,22 +851,25 @@ struct BatchUnit {
     int pad;
 };
 
+// The variants' arguments of the batch being deposited, copied from the plan's
+// workspace before each launch: read through the constant cache with a
+// CTA-uniform index, they cost the shared-memory pipe nothing.
+constexpr int kBatchMaxItems = 256;
+__constant__ DepositArgs c_batch_vars[kBatchMaxItems];
+
 template <int PIX, bool KAHAN>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
-    deposit_batched_kernel(const DepositArgs* __restrict__ vars,
-                           const BatchUnit* __restrict__ units, int n_units, int* counter) {
+    deposit_batched_kernel(const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
-    __shared__ DepositArgs s_p;   // the unit's variant arguments, read by every thread
     while (true) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
         __syncthreads();
         const int u = s_unit;
         if (u >= n_units) break;
         const BatchUnit un = units[u];
-        if (threadIdx.x == 0) s_p = vars[un.variant];
-        __syncthreads();
-        const int bits = mixed_cta<PIX, KAHAN>(s_p, un.tile, un.chunk);
-        block_status_or(s_p.status, bits);
+        const DepositArgs& p = c_batch_vars[un.variant];
+        const int bits = mixed_cta<PIX, KAHAN>(p, un.tile, un.chunk);
+        block_status_or(p.status, bits);
     }
 }
 
@@ -678,15 +889,6 @@ __global__ void zero_records_kernel(const DepositArgs* __restrict__ vars) {
         double* rec = static_cast<double*>(a.record);
         for (int64_t i = i0; i < n; i += stride) rec[i] = 0.0;
     }
-}
-
-int pick_chunk(int64_t n_e, int64_t tiles) {
-    // aim for >= 16 resident-CTA waves worth of CTAs over the 152 SMs
-    const int64_t target = (int64_t)kSms * 16;
-    int64_t chunk = (n_e * tiles + target - 1) / target;
-    if (chunk < 1) chunk = 1;
-    if (chunk > n_e) chunk = n_e;
-    return (int)chunk;
 }
 
 }  // namespace
@@ -743,9 +945,9 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
 
     if (precision == LW_FP64) {
         const int64_t tiles = (det->n_pix + kFp64Threads - 1) / kFp64Threads;
-        a.e_chunk = pick_chunk(traj->n_e, tiles);
+        a.e_chunk = (int)std::max<int64_t>(1, (traj->n_e + 65534) / 65535);
         dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
-        deposit_fp64_kernel<<<g, kFp64Threads, 0, st>>>(a);
+        deposit_fp64_jobs_kernel<<<g, kFp64Threads, 0, st>>>(a);
         return launch_status();
     }
     constexpr int PIX = kMixPix;
@@ -795,7 +997,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
                              void* stream) {
     constexpr int PIX = kMixPix;
     if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
-    if (n_items > 65535) return LW_EUNSUPPORTED;
+    if (n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
     if (precision != LW_MIXED && precision != LW_MIXED_KAHAN) return LW_EUNSUPPORTED;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     std::vector<DepositArgs> vars((size_t)n_items);
@@ -916,9 +1118,13 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     int* counter = reinterpret_cast<int*>(base + plan->offsets[0]);
     const DepositArgs* vars = reinterpret_cast<const DepositArgs*>(base + plan->offsets[1]);
     const BatchUnit* units = reinterpret_cast<const BatchUnit*>(base + plan->offsets[2]);
+    if (plan->n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
     zero_records_kernel<<<dim3(kSms * 4, (unsigned)plan->n_items), 256, 0, st>>>(vars);
     if (launch_status() != LW_OK) return LW_ECUDA;
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return LW_ECUDA;
+    if (cudaMemcpyToSymbolAsync(c_batch_vars, vars, sizeof(DepositArgs) * (size_t)plan->n_items,
+                                0, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return LW_ECUDA;
     auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, true>
                                                   : deposit_batched_kernel<PIX, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -933,6 +1139,6 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(plan->n_units, sms * per_sm);
-    kern<<<grid, kMixThreads, plan->smem_bytes, st>>>(vars, units, plan->n_units, counter);
+    kern<<<grid, kMixThreads, plan->smem_bytes, st>>>(units, plan->n_units, counter);
     return launch_status();
 }

@@ -133,13 +133,28 @@ __global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int
     const int64_t seq = seq0 + blockIdx.y;
     const int c0 = blockIdx.x * CT;
     const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
-    for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
-        const int c = t % CT, j1 = t / CT;
-        const int64_t j = (int64_t)j1 * N2 + c0 + c;
-        C z;
-        z.x = sr.ra >= 0 ? (scale * rd(sr.ra, N, j)) * scale : (T)0;
-        z.y = sr.rb >= 0 ? (scale * rd(sr.rb, N, j)) * scale : (T)0;
-        buf[bitrev(j1, logN1) * CT + c] = z;
+    // loads in batches of kBatch elements per thread, all in flight before any is stored
+    constexpr int kBatch = 8;
+    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * blockDim.x) {
+        T va[kBatch], vb[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int t = t0 + u * blockDim.x + threadIdx.x;
+            const int64_t j = (int64_t)(t / CT) * N2 + c0 + t % CT;
+            const bool in = t < N1 * CT;
+            va[u] = in && sr.ra >= 0 ? rd(sr.ra, N, j) : (T)0;
+            vb[u] = in && sr.rb >= 0 ? rd(sr.rb, N, j) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int t = t0 + u * blockDim.x + threadIdx.x;
+            if (t < N1 * CT) {
+                C z;
+                z.x = (scale * va[u]) * scale;
+                z.y = (scale * vb[u]) * scale;
+                buf[bitrev(t / CT, logN1) * CT + t % CT] = z;
+            }
+        }
     }
     __syncthreads();
     fft_smem<C>(buf, N1, logN1, CT, tw, N);

@@ -57,11 +57,11 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
         off = align256(off + sizeof(float) * 6 * (size_t)(n_e * ns1));
         L.anchor = off;
         off = align256(off + sizeof(D4) * (size_t)(n_e * L.n_blocks));
-        L.order = off;
-        off = align256(off + sizeof(int32_t) * (size_t)n_e);
-        L.order_tmp = off;   // two ordered keys (range) + kOrderBuckets counters
-        off = align256(off + 2 * sizeof(unsigned long long) + sizeof(int32_t) * kOrderBuckets);
     }
+    L.order = off;
+    off = align256(off + sizeof(int32_t) * (size_t)n_e);
+    L.order_tmp = off;   // two ordered keys (range) + kOrderBuckets counters
+    off = align256(off + 2 * sizeof(unsigned long long) + sizeof(int32_t) * kOrderBuckets);
     L.total = off;
     return L;
 }
@@ -69,7 +69,8 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
 // One pass over the samples (CTA = 256 consecutive samples of one electron;
 // grid x = sample chunks, y = electrons): input checks of every sample --
 // finite values, |beta| < 1 (evaluated as ((bx*bx + by*by) + bz*bz) < 1),
-// strictly increasing lab time -- and, when `scan` is non-null, the mixed
+// strictly increasing lab time, and with `check_steps` consecutive samples
+// closer than c0 dt (LW_ST_STEP otherwise) -- and, when `scan` is non-null, the mixed
 // section (block-relative float4, six field floats, per-block FP64 anchor).
 // The [sample][3] inputs and the [sample][6] field output are moved through
 // shared memory so that every global access is a contiguous run.
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
                    int ns1, int block_shift, int n_blocks, float4* __restrict__ scan,
-                   float* __restrict__ field, D4* __restrict__ anchor,
+                   float* __restrict__ field, D4* __restrict__ anchor, int check_steps,
                    int32_t* __restrict__ status) {
     __shared__ double s_in[3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
     __shared__ float s_out[6 * kPrepThreads];       // field records of the chunk
@@ -127,6 +128,12 @@ __global__ void __launch_bounds__(kPrepThreads)
                 if (!(bb < 1.0)) bits |= LW_ST_BETA;
             }
             if (check_t && i > 0 && !(ti > tk[i - 1])) bits |= LW_ST_TIME;
+            if (check_steps && i > 0) {   // |r_i - r_(i-1)| < c0 (t_i - t_(i-1)), in FP64
+                const double* pr = l > 0 ? &s_in[0][3 * (l - 1)] : r + 3 * (s - 1);
+                const double dx = x - pr[0], dy = y - pr[1], dz = z - pr[2];
+                const double ct = kC0 * (ti - tk[i - 1]);
+                if (!(dx * dx + dy * dy + dz * dz < ct * ct)) bits |= LW_ST_STEP;
+            }
             if (scan) {
                 const int ib = (i >> block_shift) << block_shift;
                 const int64_t sb = k * ns1 + ib;
@@ -383,9 +390,10 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
     const dim3 g((unsigned)((ns1 + kPrepThreads - 1) / kPrepThreads),
                  (unsigned)std::min<int64_t>(in->n_e, 65535));
     prepare_kernel<<<g, kPrepThreads, 0, st>>>(t, t_per_e, r, beta, bdot, in->n_e, (int)ns1, shift,
-                                          L.n_blocks, scan, field, anchor, status);
+                                          L.n_blocks, scan, field, anchor,
+                                          (sections & LW_SECTION_FP64) ? 1 : 0, status);
     if (launch_status() != LW_OK) return LW_ECUDA;
-    if (sections & LW_SECTION_MIXED) {
+    {
         int32_t* order = reinterpret_cast<int32_t*>(base + L.order);
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + L.order_tmp);
         int32_t* counts = reinterpret_cast<int32_t*>(keys + 2);

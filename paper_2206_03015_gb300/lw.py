@@ -21,7 +21,7 @@ from . import build as _build
 LW_OK, LW_EINVAL, LW_ESIZE, LW_ECUDA, LW_EUNSUPPORTED, LW_ETIMEOUT = 0, -1, -2, -3, -4, -5
 LW_FP64, LW_MIXED, LW_MIXED_KAHAN = 0, 1, 2
 LW_FIELD_ACCEL, LW_FIELD_VELOCITY = 1, 2
-LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER = 1, 2, 4, 8, 16
+LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER, LW_ST_STEP = 1, 2, 4, 8, 16, 32
 LW_SECTION_FP64, LW_SECTION_MIXED = 1, 2
 
 Q_E = 1.602176634e-19
@@ -222,10 +222,8 @@ class Trajectories:
         return self.view.n_s
 
     def order(self):
-        """The electron visiting order of the mixed deposit (int32 [n_e] view into the
-        workspace), or None without the mixed section."""
-        if not self.view.order:
-            return None
+        """The electron visiting order of the deposits (int32 [n_e] view into the
+        workspace)."""
         off = self.view.order - self.ws.data_ptr()
         return self.ws[off:off + 4 * self.n_e].view(torch.int32)
 

@@ -51,14 +51,14 @@ def test_upload_argument_checks_and_size_query(lib):
     inp = lw.lw_traj_in(10, 99, fake, 0, fake, fake, fake)
     assert lib.lw_trajectories_upload(ctypes.byref(inp), 3, 64, None, ctypes.byref(nbytes),
                                       ctypes.byref(view), None) == lw.LW_OK
-    # status + ends + FP64 copies + mixed section (scan, field, anchors, electron order
-    # and its scratch: two range keys + 4096 bucket counters), each 256-byte aligned
+    # status + ends + FP64 copies + mixed section (scan, field, anchors) + electron order
+    # and its scratch (two range keys + 4096 bucket counters), each 256-byte aligned
     ns1, ne = 100, 10
     al = lambda x: (x + 255) // 256 * 256  # noqa: E731
     fp64 = al(8 * ns1) + 3 * al(8 * 3 * ne * ns1)
-    mixed = (al(16 * ne * ns1) + al(24 * ne * ns1) + al(32 * ne * 2) + al(4 * ne)
-             + al(16 + 4 * 4096))
-    assert nbytes.value == al(4) + al(64 * ne) + fp64 + mixed
+    mixed = al(16 * ne * ns1) + al(24 * ne * ns1) + al(32 * ne * 2)
+    order = al(4 * ne) + al(16 + 4 * 4096)
+    assert nbytes.value == al(4) + al(64 * ne) + fp64 + mixed + order
     for bad_block in (8, 100, 2048):
         assert lib.lw_trajectories_upload(ctypes.byref(inp), 3, bad_block, None,
                                           ctypes.byref(nbytes), ctypes.byref(view),

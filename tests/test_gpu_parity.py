@@ -166,8 +166,12 @@ def test_upload_orders_electrons_by_first_light_front_time():
     # bucket edge: allow one bucket of disorder, nothing more
     assert np.all(np.diff(bucket[order]) >= -1)
     assert np.mean(np.diff(bucket[order]) >= 0) > 0.99
-    assert lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
-                                      sections=lw.LW_SECTION_FP64).order() is None
+    # uploads with the FP64 section only are ordered too (the order inside a bucket
+    # follows the atomics, so only the buckets' sequence is fixed)
+    other = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
+                                      sections=lw.LW_SECTION_FP64).order().cpu().numpy()
+    assert np.array_equal(np.sort(other), np.arange(tr.n_e))
+    assert np.all(np.diff(bucket[other]) >= -1)
 
 
 @pytest.mark.parametrize("precision", [lw.LW_FP64, lw.LW_MIXED])
@@ -190,3 +194,22 @@ def test_electron_chunks_accumulate_to_the_whole_deposit(precision):
     a = lw.record_value(rec, precision).cpu().numpy()
     b = lw.record_value(whole, precision).cpu().numpy()
     assert rel_l2(a, b) <= 1e-12   # the same per-electron contributions, summed in FP64
+
+
+def test_fp64_follows_algorithm_2_step_by_step_when_a_step_is_superluminal():
+    """A sampled step longer than c0 dt (the advanced time can decrease for some
+    directions): the upload flags LW_ST_STEP and the FP64 deposit follows Algorithm 2
+    step by step, repeated grid points and LW_ST_TA_ORDER included, like the oracle."""
+    tr = simple.random_smooth(3, 120, 2e-18, 17, gamma=6.0, amp=0.4)
+    r = tr.r.copy()
+    r[1, 60:, 2] += 3.0 * 299792458.0 * 2e-18     # a jump of 3 c0 dt between two samples
+    bad = simple.Trajectories(tr.t, r, tr.beta, tr.beta_dot)
+    n_hat = np.array([[0.0, 0.0, 1.0], [0.05, 0.0, math.sqrt(1 - 0.0025)]])
+    lo, hi = oracle.grid_bounds(bad.t, bad.r, n_hat)
+    grid = lw.Grid(lo, (hi - lo) / 200, 256)
+    g = gpu_run(bad, n_hat, grid, lw.LW_FP64, spectrum=False)
+    o = oracle_run(bad, n_hat, grid, spectrum=False)
+    assert g["status"] & lw.LW_ST_STEP
+    assert o["status"] & oracle.ST_TA_ORDER
+    assert (g["status"] & ~lw.LW_ST_STEP) == o["status"]
+    assert np.max(np.abs(g["rec"] - o["rec"])) <= 1e-12 * np.abs(o["rec"]).max()
