@@ -264,6 +264,10 @@ constexpr int kMaxWarpJobs = 1 << 20;
 // Jobs of a warp and block listed explicitly (slot, grid point); later ones are
 // located by bisection over the slots' job offsets.
 constexpr int kJobTable = 128;
+// Step searches: regula falsi (linear interpolation inside the bracket) for this many
+// probes, then bisection.  On the C2 trajectories it needs 2.1 probes per grid point
+// on average (at most 5); alternating interpolation and bisection needed 3.2.
+constexpr int kFalsiProbes = 8;
 
 template <bool KAHAN>
 __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
@@ -553,9 +557,10 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             // Grid point j (absolute) of slot sl: its step ends at the first sample in
             // [lo0, n-1] whose coordinate reaches fl(J - f), J = j - I (the last sample if
             // none does, at the trajectory's exact end).  Search: the bracket (a, b]
-            // starts at the block's ends; probes alternate between linear interpolation
-            // of the coordinate (near-linear over a block) and bisection, and the final
-            // bracket's two coordinates are the ones the weights need.
+            // starts at the block's ends; probes interpolate the coordinate linearly
+            // inside the bracket (regula falsi; near-linear over a block), bisection
+            // after kFalsiProbes, and the final bracket's two coordinates are the ones
+            // the weights need.
             auto job = [&](int sl, int j) {
                 const int4 jb = s_job[sl];
                 const float f = __int_as_float(jb.z);
@@ -570,15 +575,15 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     a = n - 2;
                     if (a >= 0) xa = coord(w, s32, s_scan[a]);
                 } else {
-                    bool interp = true;
+                    int probes = 0;
                     while (hb - a > 1) {
                         int g = (a + hb) >> 1;
-                        if (interp) {
+                        if (probes < kFalsiProbes) {
                             const float fr = __fdividef(tJ - xa, xb - xa);
                             const float gf = ceilf(fr * (float)(hb - a));
                             g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
                         }
-                        interp = !interp;
+                        ++probes;
                         const float xg = coord(w, s32, s_scan[g]);
                         if (xg >= tJ) {
                             hb = g;
@@ -775,15 +780,15 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
                 // first staged sample in [lo0, n-1] (local index) with u >= j
                 int a = lo0 - 1, hb = n - 1;
                 double xa = s_ua[sl], xb = s_ue[sl];
-                bool interp = true;
+                int probes = 0;
                 while (hb - a > 1) {
                     int g = (a + hb) >> 1;
-                    if (interp) {
+                    if (probes < kFalsiProbes) {
                         const float fr = __fdividef((float)(J - xa), (float)(xb - xa));
                         const float gf = ceilf(fr * (float)(hb - a));
                         g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
                     }
-                    interp = !interp;
+                    ++probes;
                     const double xg = coord64(n3, cb, g + 1);
                     if (xg >= J) {
                         hb = g;
