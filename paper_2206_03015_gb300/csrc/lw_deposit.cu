@@ -103,6 +103,75 @@ __device__ int field_fp64(double nx, double ny, double nz, double R, uint32_t fl
     return 0;
 }
 
+// State of Algorithm 2's walk over one (pixel, electron): the previous sample's
+// advanced time, coordinate and field.
+struct ScanState {
+    double tb, ub;
+    bool ok_b;
+    double Fb[3];
+    int64_t fb_step;
+    __device__ void reset() {
+        tb = ub = 0.0;
+        ok_b = false;
+        Fb[0] = Fb[1] = Fb[2] = 0.0;
+        fb_step = -1;
+    }
+};
+
+// One sample i = (t, x, y, z) of Algorithm 2's walk for the pixel (nx, ny, nz): the
+// step (t_a,i-1, t_a,i] deposits every grid point it holds, in the oracle's order.
+__device__ __forceinline__ void scan_sample(const DepositArgs& p, double nx, double ny,
+                                            double nz, double* rec, const double* bk,
+                                            const double* ak, int64_t i, double t, double x,
+                                            double y, double z, ScanState& S, int& bits) {
+    const double ta = advanced_time_fp64(nx, ny, nz, x, y, z, t);
+    const double ua = __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
+    const bool ok_a = fabs(ua) < 4.0e18;
+    if (i > 0) {
+        if (!ok_a || !S.ok_b) {
+            bits |= LW_ST_NONFINITE;
+        } else {
+            const int64_t j_hi = (int64_t)floor(ua);
+            const int64_t j_lo = (int64_t)floor(S.ub) + 1;
+            if (!(ta > S.tb)) bits |= LW_ST_TA_ORDER;
+            if (j_lo <= j_hi) {
+                int64_t ja = j_lo, jz = j_hi;
+                if (ja < 0) {
+                    ja = 0;
+                    bits |= LW_ST_CLIP;
+                }
+                if (jz > p.n_bins - 1) {
+                    jz = p.n_bins - 1;
+                    bits |= LW_ST_CLIP;
+                }
+                if (ja <= jz) {
+                    if (S.fb_step != i - 1)
+                        field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * (i - 1), ak + 3 * (i - 1),
+                                   S.Fb);
+                    double Fa[3];
+                    field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * i, ak + 3 * i, Fa);
+                    const double den = __dsub_rn(ta, S.tb);
+                    for (int64_t j = ja; j <= jz; ++j) {
+                        const double tu = __dadd_rn(p.t_min, __dmul_rn((double)j, p.dt_u));
+                        const double wa = __ddiv_rn(__dsub_rn(ta, tu), den);
+                        const double wb = __ddiv_rn(__dsub_rn(tu, S.tb), den);
+                        for (int c = 0; c < 3; ++c)
+                            atomicAdd(rec + c * p.n_bins + j,
+                                      __dadd_rn(__dmul_rn(S.Fb[c], wa), __dmul_rn(Fa[c], wb)));
+                    }
+                    S.Fb[0] = Fa[0];
+                    S.Fb[1] = Fa[1];
+                    S.Fb[2] = Fa[2];
+                    S.fb_step = i;
+                }
+            }
+        }
+    }
+    S.tb = ta;
+    S.ub = ua;
+    S.ok_b = ok_a;
+}
+
 // Algorithm 2 literally: every step of every (pixel, electron), in the oracle's
 // operation order (CTA = kFp64Threads pixels x p.e_chunk electrons).
 __device__ void fp64_scan_cta(const DepositArgs& p) {
@@ -127,10 +196,8 @@ __device__ void fp64_scan_cta(const DepositArgs& p) {
         const double* rk = p.r + 3 * k * p.ns1;
         const double* bk = p.beta + 3 * k * p.ns1;
         const double* ak = p.bdot + 3 * k * p.ns1;
-        double tb = 0.0, ub = 0.0;
-        bool ok_b = false;
-        double Fb[3] = {0.0, 0.0, 0.0};
-        int64_t fb_step = -1;
+        ScanState S;
+        S.reset();
         for (int64_t i0 = 0; i0 < p.ns1; i0 += kFp64Tile) {
             const int n = (int)min((int64_t)kFp64Tile, p.ns1 - i0);
             __syncthreads();
@@ -142,59 +209,9 @@ __device__ void fp64_scan_cta(const DepositArgs& p) {
             }
             __syncthreads();
             if (!active) continue;
-            for (int q = 0; q < n; ++q) {
-                const int64_t i = i0 + q;
-                const double ta =
-                    advanced_time_fp64(nx, ny, nz, s_r[3 * q], s_r[3 * q + 1], s_r[3 * q + 2],
-                                       s_t[q]);
-                const double ua = __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
-                const bool ok_a = fabs(ua) < 4.0e18;
-                if (i > 0) {
-                    if (!ok_a || !ok_b) {
-                        bits |= LW_ST_NONFINITE;
-                    } else {
-                        const int64_t j_hi = (int64_t)floor(ua);
-                        const int64_t j_lo = (int64_t)floor(ub) + 1;
-                        if (!(ta > tb)) bits |= LW_ST_TA_ORDER;
-                        if (j_lo <= j_hi) {
-                            int64_t ja = j_lo, jz = j_hi;
-                            if (ja < 0) {
-                                ja = 0;
-                                bits |= LW_ST_CLIP;
-                            }
-                            if (jz > p.n_bins - 1) {
-                                jz = p.n_bins - 1;
-                                bits |= LW_ST_CLIP;
-                            }
-                            if (ja <= jz) {
-                                if (fb_step != i - 1)
-                                    field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * (i - 1),
-                                               ak + 3 * (i - 1), Fb);
-                                double Fa[3];
-                                field_fp64(nx, ny, nz, p.R, p.flags, bk + 3 * i, ak + 3 * i, Fa);
-                                const double den = __dsub_rn(ta, tb);
-                                for (int64_t j = ja; j <= jz; ++j) {
-                                    const double tu =
-                                        __dadd_rn(p.t_min, __dmul_rn((double)j, p.dt_u));
-                                    const double wa = __ddiv_rn(__dsub_rn(ta, tu), den);
-                                    const double wb = __ddiv_rn(__dsub_rn(tu, tb), den);
-                                    for (int c = 0; c < 3; ++c)
-                                        atomicAdd(rec + c * p.n_bins + j,
-                                                  __dadd_rn(__dmul_rn(Fb[c], wa),
-                                                            __dmul_rn(Fa[c], wb)));
-                                }
-                                Fb[0] = Fa[0];
-                                Fb[1] = Fa[1];
-                                Fb[2] = Fa[2];
-                                fb_step = i;
-                            }
-                        }
-                    }
-                }
-                tb = ta;
-                ub = ua;
-                ok_b = ok_a;
-            }
+            for (int q = 0; q < n; ++q)
+                scan_sample(p, nx, ny, nz, rec, bk, ak, i0 + q, s_t[q], s_r[3 * q],
+                            s_r[3 * q + 1], s_r[3 * q + 2], S, bits);
         }
     }
     block_status_or(p.status, bits);
@@ -642,7 +659,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
 // it -- the step of Algorithm 2 that holds it -- and deposited with the scan's
 // FP64 expressions in the oracle's operation order, so every contribution is
 // bit-identical to the literal scan (only the order of the atomic additions
-// differs).  With LW_ST_STEP set the literal scan runs instead.
+// differs).  With LW_ST_STEP set the literal scan runs instead, and electrons that
+// reach more than half a grid point per step (on average over the CTA's pixels) are
+// walked step by step, like the scan, from the same staged blocks.
 constexpr int kF64Block = 256;   // samples staged per block
 
 __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(DepositArgs p) {
@@ -659,9 +678,11 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
     __shared__ int s_ja[kFp64Threads];              // block: first grid point of the run
     __shared__ int s_kp[kFp64Threads];              // block: job offset in the warp
     __shared__ int2 s_tab[kWarpsF][kJobTable];      // block: (slot, grid point) of job t
+    __shared__ unsigned long long s_pts[2];         // grid points of the electron (alternating)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wslot = warp * 32;
     const int64_t pix0 = (int64_t)blockIdx.x * kFp64Threads;
+    const int n_act = (int)min((int64_t)kFp64Threads, p.n_pix - pix0);
     const int64_t m = pix0 + threadIdx.x;
     const bool active = m < p.n_pix;
     const int nb = (int)p.n_bins;
@@ -714,6 +735,28 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
         if (active && !ok) bits |= LW_ST_NONFINITE;
         int64_t jdone = ok ? (int64_t)floor(u0) : 0;
         double uprev = u0;
+        // More than half a grid point per step on average over the CTA's pixels: walk
+        // every step (fields once per step, shared by the grid points it holds) instead
+        // of locating each grid point -- the choice is the CTA's, per electron.
+        const double ul = __dmul_rn(__dsub_rn(advanced_time_fp64(nx, ny, nz, e0[5], e0[6], e0[7],
+                                                                 e0[4]),
+                                              p.t_min),
+                                    p.inv_dtu);
+        unsigned long long pts = 0;
+        if (active && ok && fabs(ul) < 4.0e18) {
+            const double lo = fmax(floor(u0), -1.0), hi = fmin(floor(ul), (double)nb - 1.0);
+            if (hi > lo) pts = (unsigned long long)(hi - lo);
+        }
+        for (int o = 16; o > 0; o >>= 1) pts += __shfl_down_sync(0xffffffffu, pts, o);
+        const int ci = (int)(kk & 1);
+        if (threadIdx.x == 0) s_pts[ci] = 0;
+        __syncthreads();
+        if (lane == 0) atomicAdd(&s_pts[ci], pts);
+        __syncthreads();
+        const bool per_step = 2 * s_pts[ci] > (unsigned long long)n_act * (unsigned long long)(p.ns1 - 1);
+        ScanState S;
+        S.reset();
+        double* rec_m = static_cast<double*>(p.record) + (active ? m * 3 * p.n_bins : 0);
         for (int b = 0; b < nblk; ++b) {
             const int64_t i0 = (int64_t)b * kF64Block;
             const int n = (int)min((int64_t)kF64Block, p.ns1 - i0);
@@ -725,6 +768,14 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
                 issue(electron(kk + 1), 0, buf ^ 1);
             const int cb = buf;
             buf ^= 1;
+            if (per_step) {
+                if (active)
+                    for (int q = 1; q <= n; ++q)
+                        scan_sample(p, nx, ny, nz, rec_m, bk, ak, i0 + q - 1, s_t[cb][q],
+                                    s_r[cb][3 * q], s_r[cb][3 * q + 1], s_r[cb][3 * q + 2], S,
+                                    bits);
+                continue;
+            }
             const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
             const double ue = coord64(s_n[threadIdx.x], cb, n);
             int K = 0, ja = 0, big = 0;
