@@ -159,11 +159,13 @@ __global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int
     __syncthreads();
     fft_smem<C>(buf, N1, logN1, CT, tw, N);
     C* Ys = Y + seq * (int64_t)N;
+    // twiddle exp(2 pi i j2 l1 / N), j2 = c0 + c, as tw[c0 l1] tw[c l1]: the first factor
+    // is shared by the tile's CT columns, the second lies in the table's first CT * N1
+    // entries, which stay in cache
     for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
         const int c = t % CT, l1 = t / CT;
-        const int j2 = c0 + c;
-        const int64_t e = ((int64_t)j2 * l1) & (N - 1);
-        Ys[(int64_t)l1 * N2 + j2] = cmul(buf[l1 * CT + c], tw[e]);
+        const C w = cmul(tw[((int64_t)c0 * l1) & (N - 1)], tw[c * l1]);
+        Ys[(int64_t)l1 * N2 + c0 + c] = cmul(buf[l1 * CT + c], w);
     }
 }
 

@@ -81,6 +81,25 @@ __device__ __forceinline__ bool finite_bits(double v) {
     return ((__double2hiint(v) >> 20) & 0x7ff) != 0x7ff;
 }
 
+// double -> float, round to nearest even, on the integer pipe (IEEE 754 binary64 and
+// binary32 layouts); magnitudes below the smallest normal float become signed zero,
+// above the largest float infinity, NaN stays NaN.
+__device__ __forceinline__ float to_float(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff)
+        return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+    const int ef = e - 1023 + 127;
+    if (ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 bits
+    const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
+    unsigned f = sign | ((unsigned)ef << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ++f;   // carries into e
+    return __uint_as_float(f);
+}
+
 __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
@@ -118,8 +137,8 @@ __global__ void __launch_bounds__(kPrepThreads)
             if (!fin) bits |= LW_ST_NONFINITE;
             // |beta| < 1: decided in FP32 when 1 - beta^2 is far above its FP32 rounding,
             // else by the FP64 expression ((bx*bx + by*by) + bz*bz) < 1
-            const float b0f = (float)b0, b1f = (float)b1;
-            const float epsf = (float)(1.0 - b2);   // exact in FP64 for b2 in [0.5, 2]
+            const float b0f = to_float(b0), b1f = to_float(b1);
+            const float epsf = to_float(1.0 - b2);   // exact in FP64 for b2 in [0.5, 2]
             const float perp = fmaf(b0f, b0f, b1f * b1f);
             const float one_minus = fmaf(-epsf, epsf, 2.0f * epsf) - perp;   // 1 - beta^2
             if (!(b2 >= 0.5 && one_minus > 1.0e-5f * (2.0f * epsf + perp))) {
@@ -140,14 +159,14 @@ __global__ void __launch_bounds__(kPrepThreads)
                 const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
                 const double tau = ti - z * kInvC0;
                 const double taub = tk[ib] - zb * kInvC0;
-                scan[s] = make_float4((float)(tau - taub), (float)(x - xb), (float)(y - yb),
-                                      (float)(z - zb));
+                scan[s] = make_float4(to_float(tau - taub), to_float(x - xb), to_float(y - yb),
+                                      to_float(z - zb));
                 s_out[6 * l] = b0f;
                 s_out[6 * l + 1] = b1f;
                 s_out[6 * l + 2] = epsf;
-                s_out[6 * l + 3] = (float)a0;
-                s_out[6 * l + 4] = (float)a1;
-                s_out[6 * l + 5] = (float)a2;
+                s_out[6 * l + 3] = to_float(a0);
+                s_out[6 * l + 4] = to_float(a1);
+                s_out[6 * l + 5] = to_float(a2);
                 if (i == ib) anchor[k * n_blocks + (i >> block_shift)] = D4{taub, xb, yb, zb};
             }
         }

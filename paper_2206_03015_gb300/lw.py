@@ -221,6 +221,20 @@ class Trajectories:
     def n_s(self):
         return self.view.n_s
 
+    def mixed_section(self):
+        """(scan [n_e, n_s+1, 4], field [n_e, n_s+1, 6]) float32 views of the mixed section
+        in the workspace, or None without it."""
+        if not self.view.scan:
+            return None
+        ns1 = self.n_s + 1
+
+        def at(ptr, nbytes):
+            off = ptr - self.ws.data_ptr()
+            return self.ws[off:off + nbytes].view(torch.float32)
+        scan = at(self.view.scan, 16 * self.n_e * ns1).view(self.n_e, ns1, 4)
+        field = at(self.view.field, 24 * self.n_e * ns1).view(self.n_e, ns1, 6)
+        return scan, field
+
     def order(self):
         """The electron visiting order of the deposits (int32 [n_e] view into the
         workspace)."""

@@ -213,3 +213,25 @@ def test_fp64_follows_algorithm_2_step_by_step_when_a_step_is_superluminal():
     assert o["status"] & oracle.ST_TA_ORDER
     assert (g["status"] & ~lw.LW_ST_STEP) == o["status"]
     assert np.max(np.abs(g["rec"] - o["rec"])) <= 1e-12 * np.abs(o["rec"]).max()
+
+
+@pytest.mark.parametrize("block", [16, 512])
+def test_mixed_section_values(block):
+    """The upload's mixed section: per sample (tau - tau_b, r - r_b) rounded to FP32 from
+    FP64 differences, and (beta_x, beta_y, 1 - beta_z, beta_dot) rounded to FP32 --
+    bit-exact against numpy's round-to-nearest casts (tau to one FP64 rounding, as the
+    device may fuse the light-front product)."""
+    tr = simple.random_smooth(5, 700, 2e-18, 23, gamma=30.0, amp=0.3, t_per_electron=True)
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot, block=block)
+    scan, field = [x.cpu().numpy() for x in traj.mixed_section()]
+    ib = (np.arange(tr.n_s + 1) // block) * block
+    rb = tr.r[:, ib, :]
+    for c in range(3):
+        assert np.array_equal(scan[..., 1 + c], (tr.r[..., c] - rb[..., c]).astype(np.float32))
+    tau = tr.t - tr.r[..., 2] / 299792458.0
+    dtau = tau - tau[:, ib]
+    assert np.all(np.abs(scan[..., 0] - dtau) <= 4e-16 * np.abs(tau) + 1e-7 * np.abs(dtau))
+    assert np.array_equal(field[..., 0], tr.beta[..., 0].astype(np.float32))
+    assert np.array_equal(field[..., 1], tr.beta[..., 1].astype(np.float32))
+    assert np.array_equal(field[..., 2], (1.0 - tr.beta[..., 2]).astype(np.float32))
+    assert np.array_equal(field[..., 3:], tr.beta_dot.astype(np.float32))
