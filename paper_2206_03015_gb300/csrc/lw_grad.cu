@@ -156,7 +156,8 @@ struct AdjArgs {
 constexpr int kAdjThreads = 128;
 constexpr int kAdjTile = 64;
 
-// acceleration field (same formula and order as the FP64 forward kernel)
+// acceleration field (the FP64 forward kernel's formula; one reciprocal of D^3 instead
+// of three divisions -- the adjoint needs the field, not its last bit)
 __device__ void field_acc_fp64(double nx, double ny, double nz, const double* __restrict__ b,
                                const double* __restrict__ a, double F[3]) {
     const double b0 = b[0], b1 = b[1], b2v = b[2];
@@ -171,9 +172,10 @@ __device__ void field_acc_fp64(double nx, double ny, double nz, const double* __
     const double i0 = __dsub_rn(__dmul_rn(m1, a[2]), __dmul_rn(m2, a[1]));
     const double i1 = __dsub_rn(__dmul_rn(m2, a[0]), __dmul_rn(m0, a[2]));
     const double i2 = __dsub_rn(__dmul_rn(m0, a[1]), __dmul_rn(m1, a[0]));
-    F[0] = __ddiv_rn(__dsub_rn(__dmul_rn(ny, i2), __dmul_rn(nz, i1)), D3);
-    F[1] = __ddiv_rn(__dsub_rn(__dmul_rn(nz, i0), __dmul_rn(nx, i2)), D3);
-    F[2] = __ddiv_rn(__dsub_rn(__dmul_rn(nx, i1), __dmul_rn(ny, i0)), D3);
+    const double iD3 = 1.0 / D3;
+    F[0] = __dsub_rn(__dmul_rn(ny, i2), __dmul_rn(nz, i1)) * iD3;
+    F[1] = __dsub_rn(__dmul_rn(nz, i0), __dmul_rn(nx, i2)) * iD3;
+    F[2] = __dsub_rn(__dmul_rn(nx, i1), __dmul_rn(ny, i0)) * iD3;
 }
 
 // (dL/dF, dL/dt_a) of one sample -> (dL/dr, dL/dbeta, dL/dbdot)
@@ -282,10 +284,11 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_kernel(AdjArgs p) {
                         double Fa[3];
                         field_acc_fp64(nx, ny, nz, bk + 3 * i, ak + 3 * i, Fa);
                         const double den = __dsub_rn(ta, tb);
+                        const double iden = 1.0 / den;   // one division per step
                         for (int64_t j = ja; j <= jz; ++j) {
                             const double tu = __dadd_rn(p.t_min, __dmul_rn((double)j, p.dt_u));
-                            const double wa = __ddiv_rn(__dsub_rn(ta, tu), den);
-                            const double wb = __ddiv_rn(__dsub_rn(tu, tb), den);
+                            const double wa = __dsub_rn(ta, tu) * iden;
+                            const double wb = __dsub_rn(tu, tb) * iden;
                             const double R0 = R[j], R1 = R[p.n_bins + j], R2 = R[2 * p.n_bins + j];
                             Gc[0] += R0 * wa;
                             Gc[1] += R1 * wa;
@@ -295,8 +298,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_kernel(AdjArgs p) {
                             Gn[2] += R2 * wb;
                             const double dw = R0 * (Fa[0] - Fb[0]) + R1 * (Fa[1] - Fb[1]) +
                                               R2 * (Fa[2] - Fb[2]);
-                            gtn -= dw * wb / den;
-                            gtc -= dw * wa / den;
+                            gtn -= dw * wb * iden;
+                            gtc -= dw * wa * iden;
                         }
                         nzc = true;
                         nzn = true;

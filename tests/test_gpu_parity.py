@@ -235,3 +235,30 @@ def test_mixed_section_values(block):
     assert np.array_equal(field[..., 1], tr.beta[..., 1].astype(np.float32))
     assert np.array_equal(field[..., 2], (1.0 - tr.beta[..., 2]).astype(np.float32))
     assert np.array_equal(field[..., 3:], tr.beta_dot.astype(np.float32))
+
+
+def test_config3_mixed_spectrum_per_band():
+    """Config 3 (the mixed path on config 1's inputs): spectrum relative L2 error against
+    the FP64 oracle in the band of the Doppler fundamental omega_1(theta) +-20 % of every
+    pixel (<= 1e-4) and in the 2nd-harmonic band, where the on-axis line is weak for
+    linear polarisation and the relative error is expected to be larger (<= 1e-2)."""
+    from workloads.planewave import doppler_fundamental
+    w = configs.c1_tiny()
+    tr = w.traj
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot)
+    det = lw.Detector(w.n_hat)
+    b = lw.lw_grid_bounds(traj, det).cpu().numpy()
+    grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
+    S = lw.lw_spectrum(lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED), lw.LW_MIXED,
+                       det.n_pix, grid).double().cpu().numpy()
+    rec, _ = oracle.tdm_deposit(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat, grid.t_min,
+                                grid.dt_u, grid.n_bins)
+    S_o = oracle.spectrum(rec, grid.dt_u)
+    omega = 2 * math.pi * np.arange(grid.n_bins // 2 + 1) / (grid.n_bins * grid.dt_u)
+    theta = np.arccos(np.clip(w.n_hat[:, 2], -1.0, 1.0))
+    w1 = np.array([doppler_fundamental(w.gamma, w.lam, w.a0, th) for th in theta])
+    for h, tol in ((1.0, 1e-4), (2.0, 1e-2)):
+        band = np.abs(omega[None, :] / (h * w1[:, None]) - 1.0) <= 0.2
+        assert band.sum() > w.n_pix
+        err = np.linalg.norm((S - S_o)[band]) / np.linalg.norm(S_o[band])
+        assert err <= tol, (h, err)
