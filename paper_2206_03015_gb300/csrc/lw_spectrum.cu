@@ -41,7 +41,7 @@ template <> struct RecReader<float> {
             const float2 v = static_cast<const float2*>(rec)[row * N + j];
             return v.x + v.y;
         }
-        return (float)static_cast<const double*>(rec)[row * N + j];
+        return to_float(static_cast<const double*>(rec)[row * N + j]);   // integer pipe
     }
 };
 
@@ -169,47 +169,57 @@ __global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int
     }
 }
 
-// Pass 2: rows l1 and N1 - l1 of the three sequences of one pixel pair; transforms
-// them together and writes each spectrum value once (no atomics, no zeroing):
-// every l <= N/2 has row l mod N1, which one CTA holds as l1 or as its mirror.
+// Pass 2: rows l1 (rows consecutive values from blockIdx.x * rows, up to N1/2) and their
+// mirrors N1 - l1 of the three sequences of one pixel pair, transformed together (6 *
+// rows interleaved sequences); each spectrum value is written once (no atomics, no
+// zeroing): every l <= N/2 has row l mod N1, which one CTA holds as l1 or as a mirror.
 template <typename T>
-__global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2,
+__global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2, int rows,
                                       const typename V2<T>::type* __restrict__ tw,
                                       const typename V2<T>::type* __restrict__ Y,
                                       T* __restrict__ S, typename V2<T>::type* __restrict__ X,
                                       int64_t pair0) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][kind * 2 + (row, mirror row)]
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][column], column = (r*3 + kind)*2 + side
+    const int Cn = 6 * rows;
     const int64_t pair = pair0 + blockIdx.y;
-    const int l1 = blockIdx.x;                  // 0 .. N1/2
-    const int l1p = (N1 - l1) & (N1 - 1);       // mirror row
+    const int r0 = blockIdx.x * rows;
     const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
     const bool has1 = m1 < n_pix;
-    for (int t = threadIdx.x; t < 6 * N2; t += blockDim.x) {
-        const int col = t % 6, j2 = t / 6;
-        const int kind = col >> 1, c = col & 1;
-        const int row = c ? l1p : l1;
-        const C* Ys = Y + (pair * 3 + kind) * (int64_t)N;
-        buf[bitrev(j2, logN2) * 6 + col] = Ys[(int64_t)row * N2 + j2];
+    for (int t = threadIdx.x; t < Cn * N2; t += blockDim.x) {
+        const int j2 = t % N2, col = t / N2;
+        const int side = col & 1, kind = (col >> 1) % 3, r = col / 6;
+        const int l1 = r0 + r;
+        C v;
+        v.x = v.y = (T)0;
+        if (l1 <= N1 / 2) {
+            const int row = side ? (N1 - l1) & (N1 - 1) : l1;
+            v = Y[(pair * 3 + kind) * (int64_t)N + (int64_t)row * N2 + j2];
+        }
+        buf[bitrev(j2, logN2) * Cn + col] = v;
     }
     __syncthreads();
-    fft_smem<C>(buf, N2, logN2, 6, tw, N);
+    fft_smem<C>(buf, N2, logN2, Cn, tw, N);
     const int64_t nl = N / 2 + 1;
     const int64_t half = N / 2;
-    for (int t = threadIdx.x; t < 2 * N2; t += blockDim.x) {
-        const int c = t & 1, l2 = t >> 1;
-        if (c == 1 && l1p == l1) continue;            // self-mirrored row: once
-        const int row = c ? l1p : l1;
+    for (int t = threadIdx.x; t < 2 * rows * N2; t += blockDim.x) {
+        const int r = t % rows, side = (t / rows) & 1, l2 = t / (2 * rows);
+        const int l1 = r0 + r;
+        if (l1 > N1 / 2) continue;
+        const int l1p = (N1 - l1) & (N1 - 1);
+        if (side == 1 && l1p == l1) continue;          // self-mirrored row: once
+        const int row = side ? l1p : l1;
         const int64_t l = row + (int64_t)N1 * l2;
         if (l > half) continue;
-        // mirror index N - l lives in the other column
+        // mirror index N - l lives in the other side's column
         const int l2m = row == 0 ? (N2 - l2) & (N2 - 1) : N2 - 1 - l2;
         T pw0 = (T)0, pw1 = (T)0;
 #pragma unroll
         for (int kind = 0; kind < 3; ++kind) {
-            const C zl = buf[l2 * 6 + kind * 2 + c];
-            const C zn = buf[l2m * 6 + kind * 2 + (1 - c)];
+            const int col = (r * 3 + kind) * 2;
+            const C zl = buf[l2 * Cn + col + side];
+            const C zn = buf[l2m * Cn + col + (1 - side)];
             C A, B;   // spectra of the two real rows of the sequence
             A.x = (T)0.5 * (zl.x + zn.x);
             A.y = (T)0.5 * (zl.y - zn.y);
@@ -323,17 +333,21 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
         }
     }
     {
-        const size_t smem = sizeof(C) * (size_t)N2 * 6;
+        // rows of pass 2 per CTA: up to 4, within 96 KB of shared memory
+        int rows = 4;
+        while (rows > 1 && sizeof(C) * (size_t)N2 * 6 * rows > 96 * 1024) rows >>= 1;
+        const size_t smem = sizeof(C) * (size_t)N2 * 6 * rows;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(spectrum_pass2_kernel<T>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return LW_ECUDA;
+        const int groups = (N1 / 2 + 1 + rows - 1) / rows;
         for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
             const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
-            dim3 grid((unsigned)(N1 / 2 + 1), (unsigned)np);
-            spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw,
-                                                              Y, S, X, p0);
+            dim3 grid((unsigned)groups, (unsigned)np);
+            spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, rows,
+                                                              tw, Y, S, X, p0);
             if (launch_status() != LW_OK) return LW_ECUDA;
         }
         return LW_OK;

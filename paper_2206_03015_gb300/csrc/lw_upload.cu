@@ -81,24 +81,6 @@ __device__ __forceinline__ bool finite_bits(double v) {
     return ((__double2hiint(v) >> 20) & 0x7ff) != 0x7ff;
 }
 
-// double -> float, round to nearest even, on the integer pipe (IEEE 754 binary64 and
-// binary32 layouts); magnitudes below the smallest normal float become signed zero,
-// above the largest float infinity, NaN stays NaN.
-__device__ __forceinline__ float to_float(double v) {
-    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    if (e == 0x7ff)
-        return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
-    const int ef = e - 1023 + 127;
-    if (ef <= 0) return __uint_as_float(sign);
-    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 bits
-    const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
-    unsigned f = sign | ((unsigned)ef << 23) | m;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ++f;   // carries into e
-    return __uint_as_float(f);
-}
 
 __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
