@@ -326,21 +326,6 @@ __device__ __forceinline__ int last_point(float x, float f) {
 
 // Asynchronous global -> shared copies (LDGSTS): the next block of samples is
 // staged while the current one is processed.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 // One staging buffer: B float4 samples and B+1 field records (the block's
 // samples preceded by the previous block's last one).
 __host__ __device__ constexpr size_t stage_bytes(int B) {

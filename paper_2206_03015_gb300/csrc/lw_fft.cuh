@@ -34,6 +34,21 @@ __device__ __forceinline__ unsigned bitrev(unsigned x, int bits) {
     return __brev(x) >> (32 - bits);
 }
 
+// Shared-memory slot of element j of sequence c in a buffer of CN interleaved sequences:
+// j * CN + c, plus (PAD) one padding slot per 2^sh elements.  With sh = logL - 5 the 32
+// rows that a warp's bit-reversed stores of 32 consecutive inputs hit (they differ in the
+// top five bits of j) start on 32 different banks modulo the odd factor s * CN + 1, so
+// those stores are conflict-free; consecutive rows stay contiguous for the passes.
+__host__ __device__ __forceinline__ int fft_pad_shift(int logL) { return logL > 5 ? logL - 5 : 0; }
+template <int CN, bool PAD>
+__device__ __forceinline__ int fft_slot(int j, int c, int sh) {
+    return j * CN + (PAD ? (j >> sh) : 0) + c;
+}
+// slots a padded buffer of L rows of Cn sequences needs
+__host__ __device__ __forceinline__ int fft_slots(int L, int logL, int Cn) {
+    return L * Cn + (L >> fft_pad_shift(logL));
+}
+
 // twiddle table tw[t] = exp(+2 pi i t / N), t = 0..N-1, evaluated in FP64
 template <typename T>
 __global__ void twiddle_kernel(typename V2<T>::type* tw, int64_t N) {
@@ -48,100 +63,106 @@ __global__ void twiddle_kernel(typename V2<T>::type* tw, int64_t N) {
     }
 }
 
-// In-place radix-2 transform of C interleaved sequences of length L stored
-// as buf[j * C + c] in bit-reversed order, evaluated R <= 4 radix-2 stages at
-// a time: a pass over stages s .. s+R-1 gives each thread a group of 2^R
-// elements i0 + m h (h = 2^(s-1), m = 0 .. 2^R - 1) held in registers.  In stage
-// s+t the element m pairs with m + 2^t under the twiddle exp(2 pi i q / 2^(s+t)),
-// q = q0 + (m mod 2^t) h, q0 = the group's offset in its block; this factors
-// into the table value tw[q0 * N / 2^(s+t)] (tw[x] = exp(2 pi i x / N)) times
-// the constant root exp(2 pi i (m mod 2^t) / 2^(t+1)).  Per pass a group makes
-// 2^R reads and writes of shared memory and R table reads.  fft_smem picks R per
+// In-place transform (sign +) of CN interleaved sequences of length L held in
+// bit-reversed order at buf[fft_slot<CN, PAD>(j, c, sh)], as passes over R <= 4 radix-2
+// stages at a time.  A pass over stages s .. s+R-1 gives each thread a group of G = 2^R
+// elements x_m at i0 + m h (h = 2^(s-1), m = 0 .. G-1), the length-h transforms at offset
+// q0 of G consecutive blocks, block m holding the sub-sequence of offset rev_R(m) (R-bit
+// reversal).  The combined length-G h transform at q0 + k h is
+//   sum_m exp(2 pi i (q0 + k h) rev_R(m) / (G h)) x_m
+//     = sum_m exp(2 pi i k rev_R(m) / G) [exp(2 pi i q0 rev_R(m) / (G h)) x_m],
+// so each x_m is first multiplied by the table value tw[q0 rev_R(m) N / (G h)]
+// (tw[t] = exp(2 pi i t / N)) and the G-point transform of the bit-reversed group is then
+// evaluated by radix-2 stages whose roots exp(2 pi i r / 2^(t+1)) are constants:
+// 1, i and the odd eighth roots cost no or two multiplications.  fft_smem picks R per
 // transform so that the passes keep every thread busy.
-template <typename C> struct Root;
-template <> struct Root<double2> {
-    // exp(2 pi i k / 16), k = 0..15 (cos and sin of multiples of pi/8)
-    __device__ static double2 get(int k) {
-        constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173;
-        constexpr double c2 = 0.70710678118654752440;
-        const double cs[5] = {1.0, c1, c2, s1, 0.0};   // cos(k pi/8), k = 0..4
-        const int kk = k & 15;
-        const int q = kk & 3, o = kk >> 2;             // k = 4 o + q
-        // (cos, sin) of (q pi / 8), rotated by o quarter turns
-        const double c = cs[q], s = cs[4 - q];
-        double2 r;
-        if (o == 0) { r.x = c; r.y = s; }
-        else if (o == 1) { r.x = -s; r.y = c; }
-        else if (o == 2) { r.x = -c; r.y = -s; }
-        else { r.x = s; r.y = -c; }
-        return r;
-    }
-};
-template <> struct Root<float2> {
-    __device__ static float2 get(int k) {
-        const double2 d = Root<double2>::get(k);
-        return make_float2((float)d.x, (float)d.y);
-    }
-};
+__host__ __device__ constexpr int rev_bits(int m, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((m >> b) & 1) << (bits - 1 - b);
+    return r;
+}
 
-template <typename C, int R>
-__device__ __forceinline__ void fft_pass(C* buf, int L, int Cn, int s, const C* __restrict__ tw,
-                                         int64_t N) {
+// x * exp(2 pi i k / 16), k = 0..7 (k is a constant once the stage loops are unrolled)
+template <typename C>
+__device__ __forceinline__ C mul_root16(C x, int k) {
+    using T = decltype(x.x);
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;   // cos, sin pi/8
+    const T r2 = (T)0.70710678118654752440;                                     // sqrt(1/2)
+    C y;
+    switch (k) {
+        case 0: return x;
+        case 4: y.x = -x.y; y.y = x.x; return y;                          // i
+        case 2: y.x = (x.x - x.y) * r2; y.y = (x.x + x.y) * r2; return y;   // (1 + i)/sqrt 2
+        case 6: y.x = -(x.x + x.y) * r2; y.y = (x.x - x.y) * r2; return y;  // (-1 + i)/sqrt 2
+        case 1: return cmul(x, C{c1, s1});
+        case 3: return cmul(x, C{s1, c1});
+        case 5: return cmul(x, C{-s1, c1});
+        default: return cmul(x, C{-c1, s1});                               // k = 7
+    }
+}
+
+template <typename C, int CN, bool PAD, int R>
+__device__ __forceinline__ void fft_pass(C* buf, int L, int sh, int s, const C* __restrict__ tw,
+                                         int N) {
     constexpr int G = 1 << R;
     const int h = 1 << (s - 1);
-    const int ng = (L >> R) * Cn;
+    const int ng = (L >> R) * CN;
+    const int tstep = N >> (R + s - 1);   // table step of exp(2 pi i / (G h))
     for (int t = threadIdx.x; t < ng; t += blockDim.x) {
-        const int c = t % Cn;
-        const int g = t / Cn;
+        const int c = t % CN;
+        const int g = t / CN;
         const int q0 = g & (h - 1);
         const int i0 = ((g >> (s - 1)) << (s - 1 + R)) + q0;
         C x[G];
 #pragma unroll
-        for (int m = 0; m < G; ++m) x[m] = buf[(i0 + m * h) * Cn + c];
+        for (int m = 0; m < G; ++m) x[m] = buf[fft_slot<CN, PAD>(i0 + m * h, c, sh)];
+        if (h > 1) {   // uniform; the pre-twiddles are all 1 in the first pass
+            const int b = q0 * tstep;
+#pragma unroll
+            for (int m = 1; m < G; ++m) x[m] = cmul(x[m], tw[b * rev_bits(m, R)]);
+        }
 #pragma unroll
         for (int st = 0; st < R; ++st) {
-            const C wb = tw[(int64_t)q0 * (N >> (s + st))];
             const int half = 1 << st;
 #pragma unroll
             for (int m = 0; m < G; ++m) {
                 if (m & half) continue;
-                const int r = m & (half - 1);
-                // constant root exp(2 pi i r / 2^(st+1)) = 16th root number r * 8 / half
-                const C w = r == 0 ? wb : cmul(wb, Root<C>::get(r * (8 >> st)));
-                const C v = cmul(x[m + half], w);
+                // root exp(2 pi i r / 2^(st+1)) = 16th root number r * 8 / half
+                const C v = mul_root16(x[m + half], (m & (half - 1)) * (8 >> st));
                 const C u = x[m];
                 x[m] = cadd(u, v);
                 x[m + half] = csub(u, v);
             }
         }
 #pragma unroll
-        for (int m = 0; m < G; ++m) buf[(i0 + m * h) * Cn + c] = x[m];
+        for (int m = 0; m < G; ++m) buf[fft_slot<CN, PAD>(i0 + m * h, c, sh)] = x[m];
     }
     __syncthreads();
 }
 
 // Passes of R stages, R the largest of 2..4 that still gives every thread of the
-// CTA a group ((L >> R) * Cn >= blockDim.x), the remaining stages first.
-template <typename C>
-__device__ void fft_smem(C* buf, int L, int logL, int Cn, const C* __restrict__ tw, int64_t N) {
+// CTA a group ((L >> R) * CN >= blockDim.x), the remaining stages first.  sh is the
+// padding shift of a PAD layout (fft_slot).
+template <typename C, int CN, bool PAD>
+__device__ void fft_smem(C* buf, int L, int logL, const C* __restrict__ tw, int N, int sh = 0) {
     int R = 4;
-    while (R > 2 && (int64_t)(L >> R) * Cn < (int64_t)blockDim.x) --R;
+    while (R > 2 && (L >> R) * CN < (int)blockDim.x) --R;
     if (R > logL) R = logL;
     int s = 1;
     const int lead = R > 0 ? logL % R : 0;
-    if (lead == 1) fft_pass<C, 1>(buf, L, Cn, s, tw, N);
-    if (lead == 2) fft_pass<C, 2>(buf, L, Cn, s, tw, N);
-    if (lead == 3) fft_pass<C, 3>(buf, L, Cn, s, tw, N);
+    if (lead == 1) fft_pass<C, CN, PAD, 1>(buf, L, sh, s, tw, N);
+    if (lead == 2) fft_pass<C, CN, PAD, 2>(buf, L, sh, s, tw, N);
+    if (lead == 3) fft_pass<C, CN, PAD, 3>(buf, L, sh, s, tw, N);
     s += lead;
     for (; s <= logL; s += R) {
         if (R == 4)
-            fft_pass<C, 4>(buf, L, Cn, s, tw, N);
+            fft_pass<C, CN, PAD, 4>(buf, L, sh, s, tw, N);
         else if (R == 3)
-            fft_pass<C, 3>(buf, L, Cn, s, tw, N);
+            fft_pass<C, CN, PAD, 3>(buf, L, sh, s, tw, N);
         else if (R == 2)
-            fft_pass<C, 2>(buf, L, Cn, s, tw, N);
+            fft_pass<C, CN, PAD, 2>(buf, L, sh, s, tw, N);
         else
-            fft_pass<C, 1>(buf, L, Cn, s, tw, N);
+            fft_pass<C, CN, PAD, 1>(buf, L, sh, s, tw, N);
     }
 }
 

@@ -86,7 +86,7 @@ __global__ void adj_direct_kernel(AdjLoader ld, int N, int logN, const double2* 
     const int64_t pair = blockIdx.x;
     for (int l = threadIdx.x; l < N; l += blockDim.x) buf[bitrev(l, logN)] = ld(pair, l, N);
     __syncthreads();
-    fft_smem<double2>(buf, N, logN, 1, tw, N);
+    fft_smem<double2, 1, false>(buf, N, logN, tw, N);
     for (int j = threadIdx.x; j < N; j += blockDim.x) adj_store(out, ld.rows, pair, N, j, buf[j]);
 }
 
@@ -102,7 +102,7 @@ __global__ void adj_pass1_kernel(AdjLoader ld, int N, int N1, int logN1, int N2,
         buf[bitrev(n1, logN1) * CT + c] = ld(pair, (int64_t)n1 * N2 + c0 + c, N);
     }
     __syncthreads();
-    fft_smem<double2>(buf, N1, logN1, CT, tw, N);
+    fft_smem<double2, CT, false>(buf, N1, logN1, tw, N);
     double2* Yp = Y + pair * (int64_t)N;
     for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
         const int c = t % CT, k1 = t / CT;
@@ -126,7 +126,7 @@ __global__ void adj_pass2_kernel(int64_t rows, int N, int N1, int N2, int logN2,
         buf[bitrev(n2, logN2) * CT + c] = Yp[(int64_t)(k10 + c) * N2 + n2];
     }
     __syncthreads();
-    fft_smem<double2>(buf, N2, logN2, CT, tw, N);
+    fft_smem<double2, CT, false>(buf, N2, logN2, tw, N);
     for (int t = threadIdx.x; t < N2 * CT; t += blockDim.x) {
         const int c = t % CT, k2 = t / CT;
         adj_store(out, rows, pair, N, (int64_t)(k10 + c) + (int64_t)N1 * k2, buf[k2 * CT + c]);

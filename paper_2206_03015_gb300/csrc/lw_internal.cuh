@@ -48,23 +48,54 @@ __device__ __forceinline__ void block_status_or(int32_t* st, int bits) {
     }
 }
 
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): issued without
+// holding registers, completed by cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+// 8- and 16-byte copies that write zeros instead when !valid (src-size 0 reads nothing)
+__device__ __forceinline__ void cp_async8_zfill(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+
 // double -> float, round to nearest even, on the integer pipe (IEEE 754 binary64 and
 // binary32 layouts); magnitudes below the smallest normal float become signed zero,
 // above the largest float infinity, NaN stays NaN.
-__device__ __forceinline__ float to_float(double v) {
-    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+__device__ __forceinline__ float to_float_bits(unsigned hi, unsigned lo) {
     const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    if (e == 0x7ff)
-        return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
-    const int ef = e - 1023 + 127;
-    if (ef <= 0) return __uint_as_float(sign);
-    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 bits
-    const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
-    unsigned f = sign | ((unsigned)ef << 23) | m;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ++f;   // carries into e
-    return __uint_as_float(f);
+    const unsigned a = hi & 0x7fffffffu;   // biased exponent and the top 20 mantissa bits
+    // rebias 1023 -> 127 and keep the top 23 of the 52 mantissa bits
+    unsigned f = ((a - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;   // the 29 dropped bits
+    f += (unsigned)(rest > 0x10000000u) | ((unsigned)(rest == 0x10000000u) & f & 1u);   // carries
+    // selects, not branches, so that loads ahead of a conversion stay in flight
+    f = a < (897u << 20) ? 0u : f;   // below the smallest normal float
+    const unsigned big = a > 0x7ff00000u || (a == 0x7ff00000u && lo) ? 0x7fc00000u : 0x7f800000u;
+    f = a >= (1151u << 20) ? big : f;   // beyond the largest float, infinity or NaN
+    return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ float to_float(double v) {
+    return to_float_bits((unsigned)__double2hiint(v), (unsigned)__double2loint(v));
 }
 
 // Far-field advanced time t_a = t - (n . r) / c0 in FP64 with the documented

@@ -26,22 +26,31 @@
 namespace lw {
 namespace {
 
+// Record readers.  load() fetches an element's raw bits, cvt() turns them into T; pass 1
+// issues a batch of loads before it converts any, so that they are all in flight.
 template <typename T> struct RecReader;
 template <> struct RecReader<double> {
+    using Raw = double;
     const double* rec;
+    __device__ double load(int64_t row, int64_t N, int64_t j) const { return __ldcs(rec + row * N + j); }
+    __device__ double cvt(double v) const { return v; }
     __device__ double operator()(int64_t row, int64_t N, int64_t j) const {
-        return rec[row * N + j];
+        return cvt(load(row, N, j));
     }
 };
 template <> struct RecReader<float> {
+    using Raw = uint2;   // a double, or a (sum, compensation) float pair
     const void* rec;
     int kahan;   // 1: (sum, compensation) float pairs, 0: double
+    __device__ uint2 load(int64_t row, int64_t N, int64_t j) const {
+        return __ldcs(static_cast<const uint2*>(rec) + row * N + j);
+    }
+    __device__ float cvt(uint2 v) const {
+        if (kahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
+        return to_float_bits(v.y, v.x);   // little-endian double: v.y holds the high word
+    }
     __device__ float operator()(int64_t row, int64_t N, int64_t j) const {
-        if (kahan) {
-            const float2 v = static_cast<const float2*>(rec)[row * N + j];
-            return v.x + v.y;
-        }
-        return to_float(static_cast<const double*>(rec)[row * N + j]);   // integer pipe
+        return cvt(load(row, N, j));
     }
 };
 
@@ -98,7 +107,8 @@ __global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, in
                                        T* __restrict__ S, typename V2<T>::type* __restrict__ X) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* buf = reinterpret_cast<C*>(smem_raw);   // padded layout (fft_slot)
+    const int sh = fft_pad_shift(logN);
     const int64_t pair = blockIdx.x;
     const int64_t nl = N / 2 + 1;
     for (int kind = 0; kind < 3; ++kind) {
@@ -108,13 +118,14 @@ __global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, in
             C z;
             z.x = sr.ra >= 0 ? (scale * rd(sr.ra, N, j)) * scale : (T)0;
             z.y = sr.rb >= 0 ? (scale * rd(sr.rb, N, j)) * scale : (T)0;
-            buf[bitrev(j, logN)] = z;
+            buf[fft_slot<1, true>(bitrev(j, logN), 0, sh)] = z;
         }
         __syncthreads();
-        fft_smem<C>(buf, N, logN, 1, tw, N);
+        fft_smem<C, 1, true>(buf, N, logN, tw, N, sh);
         for (int l = threadIdx.x; l < nl; l += blockDim.x) {
             const int ln = (N - l) & (N - 1);
-            emit<T, C>(sr, l, buf[l], buf[ln], nl, S, X, false);
+            emit<T, C>(sr, l, buf[fft_slot<1, true>(l, 0, sh)], buf[fft_slot<1, true>(ln, 0, sh)], nl, S, X,
+                       false);
         }
         __syncthreads();
     }
@@ -124,93 +135,118 @@ __global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, in
 
 // Pass 1: tile of N1 rows x CT columns (columns j2 in [c0, c0+CT)) of sequence seq.
 template <typename T, int CT>
-__global__ void spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N1, int logN1,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N1, int logN1,
                                       int N2, T scale, const typename V2<T>::type* __restrict__ tw,
                                       typename V2<T>::type* __restrict__ Y, int64_t seq0) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);   // [N1][CT]
+    C* wrow = buf + N1 * CT;                    // [N1]
     const int64_t seq = seq0 + blockIdx.y;
     const int c0 = blockIdx.x * CT;
     const SeqRows sr = seq_rows(seq / 3, (int)(seq % 3), n_pix);
-    // loads in batches of kBatch elements per thread, all in flight before any is stored
+    // loads in batches of kBatch elements per thread, all in flight before any is converted
     constexpr int kBatch = 8;
+    using Raw = typename RecReader<T>::Raw;
     for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * blockDim.x) {
-        T va[kBatch], vb[kBatch];
+        Raw va[kBatch], vb[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int t = t0 + u * blockDim.x + threadIdx.x;
             const int64_t j = (int64_t)(t / CT) * N2 + c0 + t % CT;
             const bool in = t < N1 * CT;
-            va[u] = in && sr.ra >= 0 ? rd(sr.ra, N, j) : (T)0;
-            vb[u] = in && sr.rb >= 0 ? rd(sr.rb, N, j) : (T)0;
+            va[u] = in && sr.ra >= 0 ? rd.load(sr.ra, N, j) : Raw{};
+            vb[u] = in && sr.rb >= 0 ? rd.load(sr.rb, N, j) : Raw{};
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int t = t0 + u * blockDim.x + threadIdx.x;
             if (t < N1 * CT) {
                 C z;
-                z.x = (scale * va[u]) * scale;
-                z.y = (scale * vb[u]) * scale;
+                z.x = (scale * rd.cvt(va[u])) * scale;
+                z.y = (scale * rd.cvt(vb[u])) * scale;
                 buf[bitrev(t / CT, logN1) * CT + t % CT] = z;
             }
         }
     }
+    // first twiddle factor tw[c0 l1] of each row, shared by the tile's CT columns
+    for (int l1 = threadIdx.x; l1 < N1; l1 += blockDim.x)
+        wrow[l1] = tw[((int64_t)c0 * l1) & (N - 1)];
     __syncthreads();
-    fft_smem<C>(buf, N1, logN1, CT, tw, N);
+    fft_smem<C, CT, false>(buf, N1, logN1, tw, N);
     C* Ys = Y + seq * (int64_t)N;
-    // twiddle exp(2 pi i j2 l1 / N), j2 = c0 + c, as tw[c0 l1] tw[c l1]: the first factor
-    // is shared by the tile's CT columns, the second lies in the table's first CT * N1
-    // entries, which stay in cache
-    for (int t = threadIdx.x; t < N1 * CT; t += blockDim.x) {
-        const int c = t % CT, l1 = t / CT;
-        const C w = cmul(tw[((int64_t)c0 * l1) & (N - 1)], tw[c * l1]);
-        Ys[(int64_t)l1 * N2 + c0 + c] = cmul(buf[l1 * CT + c], w);
+    // twiddle exp(2 pi i j2 l1 / N), j2 = c0 + c, as tw[c0 l1] tw[c l1]: the second factor
+    // lies in the table's first CT * N1 entries, which stay in cache
+    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * blockDim.x) {
+        C w2[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int t = t0 + u * blockDim.x + threadIdx.x;
+            w2[u] = t < N1 * CT ? tw[(t % CT) * (t / CT)] : C{};
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int t = t0 + u * blockDim.x + threadIdx.x;
+            if (t < N1 * CT) {
+                const int c = t % CT, l1 = t / CT;
+                __stcs(Ys + (int64_t)l1 * N2 + c0 + c, cmul(buf[l1 * CT + c], cmul(wrow[l1], w2[u])));
+            }
+        }
     }
 }
 
-// Pass 2: rows l1 (rows consecutive values from blockIdx.x * rows, up to N1/2) and their
+// Pass 2: rows l1 (ROWS consecutive values from blockIdx.x * ROWS, up to N1/2) and their
 // mirrors N1 - l1 of the three sequences of one pixel pair, transformed together (6 *
-// rows interleaved sequences); each spectrum value is written once (no atomics, no
+// ROWS interleaved sequences); each spectrum value is written once (no atomics, no
 // zeroing): every l <= N/2 has row l mod N1, which one CTA holds as l1 or as a mirror.
-template <typename T>
-__global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2, int rows,
-                                      const typename V2<T>::type* __restrict__ tw,
-                                      const typename V2<T>::type* __restrict__ Y,
-                                      T* __restrict__ S, typename V2<T>::type* __restrict__ X,
-                                      int64_t pair0) {
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+    spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2,
+                          const typename V2<T>::type* __restrict__ tw,
+                          const typename V2<T>::type* __restrict__ Y, T* __restrict__ S,
+                          typename V2<T>::type* __restrict__ X, int64_t pair0) {
     using C = typename V2<T>::type;
+    constexpr int Cn = 6 * ROWS;   // column = (r*3 + kind)*2 + side
     extern __shared__ unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][column], column = (r*3 + kind)*2 + side
-    const int Cn = 6 * rows;
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][Cn], padded (fft_slot)
+    const int sh = fft_pad_shift(logN2);
     const int64_t pair = pair0 + blockIdx.y;
-    const int r0 = blockIdx.x * rows;
+    const int r0 = blockIdx.x * ROWS;
     const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
     const bool has1 = m1 < n_pix;
+    // every element of the tile is copied straight into its bit-reversed slot by
+    // cp.async, all of them in flight at once; rows past N1/2 are zero-filled
+    const C* Yp = Y + pair * 3 * (int64_t)N;
+#pragma unroll 1
     for (int t = threadIdx.x; t < Cn * N2; t += blockDim.x) {
-        const int j2 = t % N2, col = t / N2;
+        const int j2 = t & (N2 - 1), col = t >> logN2;
         const int side = col & 1, kind = (col >> 1) % 3, r = col / 6;
         const int l1 = r0 + r;
-        C v;
-        v.x = v.y = (T)0;
-        if (l1 <= N1 / 2) {
-            const int row = side ? (N1 - l1) & (N1 - 1) : l1;
-            v = Y[(pair * 3 + kind) * (int64_t)N + (int64_t)row * N2 + j2];
-        }
-        buf[bitrev(j2, logN2) * Cn + col] = v;
+        const bool valid = l1 <= N1 / 2;
+        const int row = valid ? (side ? (N1 - l1) & (N1 - 1) : l1) : 0;
+        const C* src = Yp + (kind * N + row * N2 + j2);
+        C* dst = buf + fft_slot<Cn, true>(bitrev(j2, logN2), col, sh);
+        if (sizeof(C) == 8)
+            cp_async8_zfill(dst, src, valid);
+        else
+            cp_async16_zfill(dst, src, valid);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    fft_smem<C>(buf, N2, logN2, Cn, tw, N);
+    fft_smem<C, Cn, true>(buf, N2, logN2, tw, N, sh);
     const int64_t nl = N / 2 + 1;
-    const int64_t half = N / 2;
-    for (int t = threadIdx.x; t < 2 * rows * N2; t += blockDim.x) {
-        const int r = t % rows, side = (t / rows) & 1, l2 = t / (2 * rows);
+    const int half = N / 2;
+    T* S0 = S + m0 * nl;
+    T* S1 = S + m1 * nl;
+    for (int t = threadIdx.x; t < 2 * ROWS * N2; t += blockDim.x) {
+        const int r = t % ROWS, side = (t / ROWS) & 1, l2 = t / (2 * ROWS);
         const int l1 = r0 + r;
         if (l1 > N1 / 2) continue;
         const int l1p = (N1 - l1) & (N1 - 1);
         if (side == 1 && l1p == l1) continue;          // self-mirrored row: once
         const int row = side ? l1p : l1;
-        const int64_t l = row + (int64_t)N1 * l2;
+        const int l = row + N1 * l2;
         if (l > half) continue;
         // mirror index N - l lives in the other side's column
         const int l2m = row == 0 ? (N2 - l2) & (N2 - 1) : N2 - 1 - l2;
@@ -218,8 +254,8 @@ __global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int 
 #pragma unroll
         for (int kind = 0; kind < 3; ++kind) {
             const int col = (r * 3 + kind) * 2;
-            const C zl = buf[l2 * Cn + col + side];
-            const C zn = buf[l2m * Cn + col + (1 - side)];
+            const C zl = buf[fft_slot<Cn, true>(l2, col + side, sh)];
+            const C zn = buf[fft_slot<Cn, true>(l2m, col + (1 - side), sh)];
             C A, B;   // spectra of the two real rows of the sequence
             A.x = (T)0.5 * (zl.x + zn.x);
             A.y = (T)0.5 * (zl.y - zn.y);
@@ -248,8 +284,8 @@ __global__ void spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int 
                 }
             }
         }
-        S[m0 * nl + l] = pw0;
-        if (has1) S[m1 * nl + l] = pw1;
+        S0[l] = pw0;
+        if (has1) S1[l] = pw1;
     }
 }
 
@@ -303,7 +339,7 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     if (direct) {
         if (cudaMemsetAsync(S, 0, sizeof(T) * (size_t)nl * (size_t)n_pix, st) != cudaSuccess)
             return LW_ECUDA;
-        const size_t smem = sizeof(C) * (size_t)N;
+        const size_t smem = sizeof(C) * (size_t)fft_slots((int)N, logN, 1);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(spectrum_direct_kernel<T>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -317,7 +353,7 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     const int N1 = 1 << logN1, N2 = 1 << logN2;
     constexpr int CT = 16;
     {
-        const size_t smem = sizeof(C) * (size_t)N1 * CT;
+        const size_t smem = sizeof(C) * (size_t)N1 * (CT + 1);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(spectrum_pass1_kernel<T, CT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -335,19 +371,20 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     {
         // rows of pass 2 per CTA: up to 4, within 96 KB of shared memory
         int rows = 4;
-        while (rows > 1 && sizeof(C) * (size_t)N2 * 6 * rows > 96 * 1024) rows >>= 1;
-        const size_t smem = sizeof(C) * (size_t)N2 * 6 * rows;
+        while (rows > 1 && sizeof(C) * (size_t)fft_slots(N2, logN2, 6 * rows) > 96 * 1024)
+            rows >>= 1;
+        const size_t smem = sizeof(C) * (size_t)fft_slots(N2, logN2, 6 * rows);
+        auto kern = rows == 4 ? spectrum_pass2_kernel<T, 4>
+                    : rows == 2 ? spectrum_pass2_kernel<T, 2> : spectrum_pass2_kernel<T, 1>;
         if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(spectrum_pass2_kernel<T>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return LW_ECUDA;
         const int groups = (N1 / 2 + 1 + rows - 1) / rows;
         for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
             const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
             dim3 grid((unsigned)groups, (unsigned)np);
-            spectrum_pass2_kernel<T><<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, rows,
-                                                              tw, Y, S, X, p0);
+            kern<<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw, Y, S, X, p0);
             if (launch_status() != LW_OK) return LW_ECUDA;
         }
         return LW_OK;
