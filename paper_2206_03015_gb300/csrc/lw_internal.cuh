@@ -82,17 +82,17 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, b
 // binary32 layouts); magnitudes below the smallest normal float become signed zero,
 // above the largest float infinity, NaN stays NaN.
 __device__ __forceinline__ float to_float_bits(unsigned hi, unsigned lo) {
-    const unsigned sign = hi & 0x80000000u;
     const unsigned a = hi & 0x7fffffffu;   // biased exponent and the top 20 mantissa bits
-    // rebias 1023 -> 127 and keep the top 23 of the 52 mantissa bits
-    unsigned f = ((a - (896u << 20)) << 3) | (lo >> 29);
-    const unsigned rest = lo & 0x1fffffffu;   // the 29 dropped bits
-    f += (unsigned)(rest > 0x10000000u) | ((unsigned)(rest == 0x10000000u) & f & 1u);   // carries
+    // round to nearest even at bit 29 of the magnitude's 64-bit pattern: adding half an
+    // ulp less one, plus the kept lsb, carries into bit 29 exactly when rounding up
+    unsigned long long v = ((unsigned long long)a << 32) | lo;
+    v += 0x0fffffffull + ((lo >> 29) & 1u);
+    unsigned f = (unsigned)(v >> 29) - (896u << 23);   // rebias 1023 -> 127
     // selects, not branches, so that loads ahead of a conversion stay in flight
     f = a < (897u << 20) ? 0u : f;   // below the smallest normal float
     const unsigned big = a > 0x7ff00000u || (a == 0x7ff00000u && lo) ? 0x7fc00000u : 0x7f800000u;
     f = a >= (1151u << 20) ? big : f;   // beyond the largest float, infinity or NaN
-    return __uint_as_float(sign | f);
+    return __uint_as_float((hi & 0x80000000u) | f);
 }
 __device__ __forceinline__ float to_float(double v) {
     return to_float_bits((unsigned)__double2hiint(v), (unsigned)__double2loint(v));

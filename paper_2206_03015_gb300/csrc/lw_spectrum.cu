@@ -34,6 +34,7 @@ template <> struct RecReader<double> {
     const double* rec;
     __device__ double load(int64_t row, int64_t N, int64_t j) const { return __ldcs(rec + row * N + j); }
     __device__ double cvt(double v) const { return v; }
+    __device__ double cvt_fp64(double v) const { return v; }
     __device__ double operator()(int64_t row, int64_t N, int64_t j) const {
         return cvt(load(row, N, j));
     }
@@ -45,9 +46,16 @@ template <> struct RecReader<float> {
     __device__ uint2 load(int64_t row, int64_t N, int64_t j) const {
         return __ldcs(static_cast<const uint2*>(rec) + row * N + j);
     }
-    __device__ float cvt(uint2 v) const {
+    __device__ float cvt(uint2 v) const {   // double -> float on the integer pipe
         if (kahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
         return to_float_bits(v.y, v.x);   // little-endian double: v.y holds the high word
+    }
+    // the same rounding by the FP64 pipe's conversion: pass 1 converts one row of each
+    // pair this way and one on the integer pipe, which its index work already loads
+    // (results differ only below the smallest normal float, which this one keeps)
+    __device__ float cvt_fp64(uint2 v) const {
+        if (kahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
+        return __double2float_rn(__hiloint2double((int)v.y, (int)v.x));
     }
     __device__ float operator()(int64_t row, int64_t N, int64_t j) const {
         return cvt(load(row, N, j));
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_ke
             const int t = t0 + u * blockDim.x + threadIdx.x;
             if (t < N1 * CT) {
                 C z;
-                z.x = (scale * rd.cvt(va[u])) * scale;
+                z.x = (scale * rd.cvt_fp64(va[u])) * scale;
                 z.y = (scale * rd.cvt(vb[u])) * scale;
                 buf[bitrev(t / CT, logN1) * CT + t % CT] = z;
             }

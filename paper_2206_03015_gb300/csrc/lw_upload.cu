@@ -90,9 +90,12 @@ __global__ void __launch_bounds__(kPrepThreads)
                    int32_t* __restrict__ status) {
     __shared__ double s_in[3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
     __shared__ float s_out[6 * kPrepThreads];       // field records of the chunk
+    __shared__ double s_taub[kPrepThreads];         // tau of the chunk's block starts
     int bits = 0;
     const int i_first = blockIdx.x * kPrepThreads;
     const int cnt = min(kPrepThreads, ns1 - i_first);
+    const int b_first = i_first >> block_shift;
+    const int n_b = ((i_first + cnt - 1) >> block_shift) - b_first + 1;   // blocks met
     for (int64_t k = blockIdx.y; k < n_e; k += gridDim.y) {
         const int64_t s0 = k * ns1 + i_first;
         __syncthreads();
@@ -101,8 +104,12 @@ __global__ void __launch_bounds__(kPrepThreads)
             s_in[1][q] = beta[3 * s0 + q];
             s_in[2][q] = bdot[3 * s0 + q];
         }
-        __syncthreads();
         const double* tk = t + (t_per_e ? k * ns1 : 0);
+        if (scan && threadIdx.x < n_b) {   // once per block, not per sample (FP64 pipe)
+            const int ib = (b_first + threadIdx.x) << block_shift;
+            s_taub[threadIdx.x] = tk[ib] - r[3 * (k * ns1 + ib) + 2] * kInvC0;
+        }
+        __syncthreads();
         const bool check_t = t_per_e || k == 0;
         const int l = threadIdx.x;
         if (l < cnt) {
@@ -123,7 +130,10 @@ __global__ void __launch_bounds__(kPrepThreads)
             const float epsf = to_float(1.0 - b2);   // exact in FP64 for b2 in [0.5, 2]
             const float perp = fmaf(b0f, b0f, b1f * b1f);
             const float one_minus = fmaf(-epsf, epsf, 2.0f * epsf) - perp;   // 1 - beta^2
-            if (!(b2 >= 0.5 && one_minus > 1.0e-5f * (2.0f * epsf + perp))) {
+            // b2 >= 0.5 on the bits: non-negative and exponent >= -1 (NaN goes on to the
+            // FP64 test and fails it)
+            const bool b2_half = __double2hiint(b2) >= 0x3fe00000;
+            if (!(b2_half && one_minus > 1.0e-5f * (2.0f * epsf + perp))) {
                 const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
                                             __dmul_rn(b2, b2));
                 if (!(bb < 1.0)) bits |= LW_ST_BETA;
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(kPrepThreads)
                 const int64_t sb = k * ns1 + ib;
                 const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
                 const double tau = ti - z * kInvC0;
-                const double taub = tk[ib] - zb * kInvC0;
+                const double taub = s_taub[(i >> block_shift) - b_first];
                 scan[s] = make_float4(to_float(tau - taub), to_float(x - xb), to_float(y - yb),
                                       to_float(z - zb));
                 s_out[6 * l] = b0f;
