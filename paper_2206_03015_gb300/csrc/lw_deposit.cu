@@ -250,10 +250,12 @@ struct PixelConst {
 };
 
 // Per-sample FP32 field in the stable form (zero if D <= 0).
-__device__ __forceinline__ void field_fp32(const PixelConst& pc, const float* __restrict__ f,
+// f: the sample's six field floats as three 8-byte-aligned pairs.
+__device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* __restrict__ f,
                                            uint32_t flags, float c0_over_R, float F[3]) {
-    const float bx = f[0], by = f[1], eps = f[2];
-    const float ax = f[3], ay = f[4], az = f[5];
+    const float2 f01 = f[0], f23 = f[1], f45 = f[2];
+    const float bx = f01.x, by = f01.y, eps = f23.x;
+    const float ax = f23.y, ay = f45.x, az = f45.y;
     const float D = fmaf(-pc.ny, by, fmaf(-pc.nx, bx, fmaf(pc.nz, eps, pc.omnz)));
     F[0] = F[1] = F[2] = 0.0f;
     if (!(D > 0.0f)) return;
@@ -353,10 +355,14 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     const int B = p.block;
     const size_t sbytes = stage_bytes(B);
     constexpr int kWarpsMix = kMixThreads / 32;
+    // Slot numbering: the warp's jobs are ordered lane by lane (a lane's PIX pixels in
+    // turn), so the job offsets s_kp are indexed lane-major, wslot + lane * PIX + q; the
+    // per-slot data are indexed q-major, wslot + q * 32 + lane, so that a warp's accesses
+    // to its own slots are contiguous.
     __shared__ float4 s_wh[kSlots];                            // slope hi parts (w_x, w_y, w_z)
-    __shared__ int4 s_job[kSlots];                             // block: I, first point, f, v_prev
-    __shared__ float s_xe[kSlots];                             // block: coordinate of last sample
-    __shared__ int s_kp[kSlots];                               // block: job offset in the warp
+    __shared__ int4 s_job[kSlots];                             // block: I, f, v_prev, x_end
+    __shared__ int s_ja[kSlots];                               // block: first grid point
+    __shared__ int s_kp[kSlots];                               // block: job offset (lane-major)
     __shared__ int2 s_tab[kWarpsMix][kJobTable];               // block: (slot, grid point) of job t
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -385,8 +391,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         const double sc = kInvC0 * p.inv_dtu;
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
-        const int sl = wslot + lane * PIX + q;
-        s_wh[sl] = make_float4(wx.hi, wy.hi, wz.hi, 0.0f);
+        s_wh[wslot + q * 32 + lane] = make_float4(wx.hi, wy.hi, wz.hi, 0.0f);
         wlo[q][0] = wx.lo;
         wlo[q][1] = wy.lo;
         wlo[q][2] = wz.lo;
@@ -394,10 +399,10 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     int bits = 0;
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
 
-    // pixel (global index) of slot `sl`
+    // pixel (global index) of q-major slot `sl`
     auto slot_pixel = [&](int sl) -> int64_t {
         const int w = sl / (32 * PIX), r = sl % (32 * PIX);
-        return pix0 + (r % PIX) * kMixThreads + w * 32 + r / PIX;
+        return pix0 + (r / 32) * kMixThreads + w * 32 + r % 32;
     };
     auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
     // stage block b of electron k into buffer `buf`
@@ -469,7 +474,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 issue(electron(kk + 1), 0, buf ^ 1);
             const unsigned char* base = smem_raw + buf * sbytes;
             const float4* s_scan = reinterpret_cast<const float4*>(base);
-            const float* s_field = reinterpret_cast<const float*>(base + 16 * (size_t)B);
+            const float2* s_field2 = reinterpret_cast<const float2*>(base + 16 * (size_t)B);
             buf ^= 1;
             if ((b & 31) == 0) split_anchor(k, b + lane, anc32);
             float an[8];
@@ -477,11 +482,74 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             for (int c = 0; c < 8; ++c) an[c] = __shfl_sync(0xffffffffu, anc32[c], b & 31);
             const bool last_block = (i0 + n == p.ns1);
             const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
-            int K[PIX], big[PIX];
+            // Grid point j (absolute) of slot sl (q-major) with block data I, f, v0p
+            // (coordinate of sample i0-1), xe (coordinate of the last sample) and slope w:
+            // its step ends at the first sample in [lo0, n-1] whose coordinate reaches
+            // fl(J - f), J = j - I (the last sample if none does, at the trajectory's exact
+            // end).  Search: the bracket (a, b] starts at the block's ends; probes
+            // interpolate the coordinate linearly inside the bracket (regula falsi;
+            // near-linear over a block), bisection after kFalsiProbes, and the final
+            // bracket's two coordinates are the ones the weights need.
+            auto job_core = [&](int sl, int j, int Ib, float f, float v0p, float xe, float4 w) {
+                const float J = (float)(j - Ib);
+                const float tJ = __fsub_rn(J, f);
+                int a = lo0 - 1, hb = n - 1;
+                float xa = lo0 ? coord(w, s32, s_scan[0]) : __fsub_rn(v0p, f);
+                float xb = xe;
+                if (xb < tJ) {   // beyond the FP32 coordinate of the last sample
+                    a = n - 2;
+                    if (a >= 0) xa = coord(w, s32, s_scan[a]);
+                } else {
+                    int probes = 0;
+                    while (hb - a > 1) {
+                        int g = (a + hb) >> 1;
+                        if (probes < kFalsiProbes) {
+                            const float fr = __fdividef(tJ - xa, xb - xa);
+                            const float gf = ceilf(fr * (float)(hb - a));
+                            g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
+                        }
+                        ++probes;
+                        const float xg = coord(w, s32, s_scan[g]);
+                        if (xg >= tJ) {
+                            hb = g;
+                            xb = xg;
+                        } else {
+                            a = g;
+                            xa = xg;
+                        }
+                    }
+                }
+                const int i = hb;
+                const float vi = __fadd_rn(xb, f);
+                const float vp = a >= 0 ? __fadd_rn(xa, f) : v0p;
+                const float a0 = __fsub_rn(J, vp);
+                const float du = __fsub_rn(vi, vp);
+                PixelConst pc;
+                pc.nx = -w.x * inv_sc;
+                pc.ny = -w.y * inv_sc;
+                pc.omnz = w.z * inv_sc;
+                pc.nz = 1.0f - pc.omnz;
+                float Fb[3], Fa[3];
+                field_fp32(pc, s_field2 + 3 * i, p.flags, c0_over_R, Fb);
+                field_fp32(pc, s_field2 + 3 * (i + 1), p.flags, c0_over_R, Fa);
+                const float wb = du > 0.0f ? a0 * __frcp_rn(du) : 0.0f;
+                const float wa = 1.0f - wb;
+                const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
+                accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
+                accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+                accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+            };
+            // a job handed to the warp: the slot's block data from shared memory
+            auto job = [&](int sl, int j) {
+                const int4 jb = s_job[sl];
+                job_core(sl, j, jb.x, __int_as_float(jb.y), __int_as_float(jb.z),
+                         __int_as_float(jb.w), s_wh[sl]);
+            };
+            int K[PIX], big[PIX], JA[PIX];
             int tot = 0;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
-                const int sl = wslot + lane * PIX + q;
+                const int sl = wslot + q * 32 + lane;
                 // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
                 const float4 wh = s_wh[sl];
                 const float whc[3] = {wh.x, wh.y, wh.z};
@@ -522,8 +590,10 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 }
                 if (jend > jdone[q]) jdone[q] = jend;
                 vlast[q] = __fadd_rn(xe, f);
-                s_job[sl] = make_int4(Inew, ja, __float_as_int(f), __float_as_int(v0p));
-                s_xe[sl] = xe;
+                s_job[sl] = make_int4(Inew, __float_as_int(f), __float_as_int(v0p),
+                                      __float_as_int(xe));
+                s_ja[sl] = ja;
+                JA[q] = ja;
                 big[q] = kq > kMaxWarpJobs ? kq : 0;
                 K[q] = kq > kMaxWarpJobs ? 0 : kq;
                 tot += K[q];
@@ -540,81 +610,25 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             int run = incl - tot;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
-                const int sl = wslot + lane * PIX + q;
-                s_kp[sl] = run;
-                const int ja = s_job[sl].y;
+                s_kp[wslot + lane * PIX + q] = run;
+                const int sl = wslot + q * 32 + lane;
                 for (int t = 0; t < K[q] && run + t < kJobTable; ++t)
-                    s_tab[warp][run + t] = make_int2(sl, ja + t);
+                    s_tab[warp][run + t] = make_int2(sl, JA[q] + t);
                 run += K[q];
             }
             __syncwarp();
-            // slot of the warp's job t beyond the table: the last slot whose offset is <= t
+            // slot (q-major) of the warp's job t beyond the table: the last slot whose
+            // offset is <= t (a lane-major search)
             auto slot_of = [&](int t) -> int {
                 int pos = 0;
 #pragma unroll
                 for (int step = 16 * PIX; step > 0; step >>= 1)
                     if (s_kp[wslot + pos + step] <= t) pos += step;
-                return wslot + pos;
+                return wslot + (pos % PIX) * 32 + pos / PIX;
             };
-            // Grid point j (absolute) of slot sl: its step ends at the first sample in
-            // [lo0, n-1] whose coordinate reaches fl(J - f), J = j - I (the last sample if
-            // none does, at the trajectory's exact end).  Search: the bracket (a, b]
-            // starts at the block's ends; probes interpolate the coordinate linearly
-            // inside the bracket (regula falsi; near-linear over a block), bisection
-            // after kFalsiProbes, and the final bracket's two coordinates are the ones
-            // the weights need.
-            auto job = [&](int sl, int j) {
-                const int4 jb = s_job[sl];
-                const float f = __int_as_float(jb.z);
-                const float v0p = __int_as_float(jb.w);
-                const float4 w = s_wh[sl];
-                const float J = (float)(j - jb.x);
-                const float tJ = __fsub_rn(J, f);
-                int a = lo0 - 1, hb = n - 1;
-                float xa = lo0 ? coord(w, s32, s_scan[0]) : __fsub_rn(v0p, f);
-                float xb = s_xe[sl];
-                if (xb < tJ) {   // beyond the FP32 coordinate of the last sample
-                    a = n - 2;
-                    if (a >= 0) xa = coord(w, s32, s_scan[a]);
-                } else {
-                    int probes = 0;
-                    while (hb - a > 1) {
-                        int g = (a + hb) >> 1;
-                        if (probes < kFalsiProbes) {
-                            const float fr = __fdividef(tJ - xa, xb - xa);
-                            const float gf = ceilf(fr * (float)(hb - a));
-                            g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
-                        }
-                        ++probes;
-                        const float xg = coord(w, s32, s_scan[g]);
-                        if (xg >= tJ) {
-                            hb = g;
-                            xb = xg;
-                        } else {
-                            a = g;
-                            xa = xg;
-                        }
-                    }
-                }
-                const int i = hb;
-                const float vi = __fadd_rn(xb, f);
-                const float vp = a >= 0 ? __fadd_rn(xa, f) : v0p;
-                const float a0 = __fsub_rn(J, vp);
-                const float du = __fsub_rn(vi, vp);
-                PixelConst pc;
-                pc.nx = -w.x * inv_sc;
-                pc.ny = -w.y * inv_sc;
-                pc.omnz = w.z * inv_sc;
-                pc.nz = 1.0f - pc.omnz;
-                float Fb[3], Fa[3];
-                field_fp32(pc, s_field + 6 * i, p.flags, c0_over_R, Fb);
-                field_fp32(pc, s_field + 6 * (i + 1), p.flags, c0_over_R, Fa);
-                const float wb = du > 0.0f ? a0 * __frcp_rn(du) : 0.0f;
-                const float wa = 1.0f - wb;
-                const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
-                accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
-                accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-                accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+            auto slot_offset = [&](int sl) -> int {   // s_kp entry of q-major slot sl
+                const int r = sl - wslot;
+                return s_kp[wslot + (r % 32) * PIX + r / 32];
             };
             for (int t = lane; t < T; t += 32) {
                 if (t < kJobTable) {
@@ -622,13 +636,13 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     job(e.x, e.y);
                 } else {
                     const int sl = slot_of(t);
-                    job(sl, s_job[sl].y + (t - s_kp[sl]));
+                    job(sl, s_ja[sl] + (t - slot_offset(sl)));
                 }
             }
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {   // runs too long for the warp's job count
-                const int sl = wslot + lane * PIX + q;
-                for (int t = 0; t < big[q]; ++t) job(sl, s_job[sl].y + t);
+                const int sl = wslot + q * 32 + lane;
+                for (int t = 0; t < big[q]; ++t) job(sl, JA[q] + t);
             }
             __syncwarp();   // s_job / s_kp are rewritten for the next block
         }
