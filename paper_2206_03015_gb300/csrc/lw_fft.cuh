@@ -166,5 +166,70 @@ __device__ void fft_smem(C* buf, int L, int logL, const C* __restrict__ tw, int 
     }
 }
 
+// The same transform with the length 2^LOGL, the pass plan and the layout fixed at
+// compile time, for CTAs of kFftThreads threads.  Element i0 + m h of a group is at
+// slot base + off(m) with base = i0 CN + c + (i0 >> SH) and off(m) = m h CN +
+// ((m h) >> SH): the bits of the block start, of q0 < h and of m h are disjoint, so the
+// padding shift splits over them, and every group reads and writes at immediate
+// offsets from one base.
+constexpr int kFftThreads = 256;
+
+template <int CN, int LOGL>
+__host__ __device__ constexpr int fft_fixed_radix() {
+    int R = 4;
+    while (R > 2 && ((1 << LOGL) >> R) * CN < kFftThreads) --R;
+    return R < LOGL ? R : LOGL;
+}
+
+template <typename C, int CN, bool PAD, int LOGL, int R, int S>
+__device__ __forceinline__ void fft_pass_fixed(C* buf, const C* __restrict__ tw, int N) {
+    constexpr int G = 1 << R;
+    constexpr int h = 1 << (S - 1);
+    constexpr int SH = PAD ? (LOGL > 5 ? LOGL - 5 : 0) : 31;
+    constexpr int ng = ((1 << LOGL) >> R) * CN;
+    const int tstep = N >> (R + S - 1);   // table step of exp(2 pi i / (G h))
+#pragma unroll 1
+    for (int t = threadIdx.x; t < ng; t += kFftThreads) {
+        const int c = t % CN;
+        const int g = t / CN;
+        const int q0 = g & (h - 1);
+        const int i0 = ((g >> (S - 1)) << (S - 1 + R)) + q0;
+        C* bp = buf + (i0 * CN + c + (PAD ? (i0 >> SH) : 0));
+        C x[G];
+#pragma unroll
+        for (int m = 0; m < G; ++m) x[m] = bp[m * h * CN + (PAD ? ((m * h) >> SH) : 0)];
+        if (h > 1) {
+            const int b = q0 * tstep;
+#pragma unroll
+            for (int m = 1; m < G; ++m) x[m] = cmul(x[m], tw[b * rev_bits(m, R)]);
+        }
+#pragma unroll
+        for (int st = 0; st < R; ++st) {
+            const int half = 1 << st;
+#pragma unroll
+            for (int m = 0; m < G; ++m) {
+                if (m & half) continue;
+                const C v = mul_root16(x[m + half], (m & (half - 1)) * (8 >> st));
+                const C u = x[m];
+                x[m] = cadd(u, v);
+                x[m + half] = csub(u, v);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < G; ++m) bp[m * h * CN + (PAD ? ((m * h) >> SH) : 0)] = x[m];
+    }
+    __syncthreads();
+}
+
+template <typename C, int CN, bool PAD, int LOGL, int S = 1>
+__device__ __forceinline__ void fft_smem_fixed(C* buf, const C* __restrict__ tw, int N) {
+    if constexpr (S <= LOGL) {
+        constexpr int R = fft_fixed_radix<CN, LOGL>();
+        constexpr int lead = LOGL % R;
+        constexpr int RR = (S == 1 && lead) ? lead : R;
+        fft_pass_fixed<C, CN, PAD, LOGL, RR, S>(buf, tw, N);
+        fft_smem_fixed<C, CN, PAD, LOGL, S + RR>(buf, tw, N);
+    }
+}
 
 }  // namespace lw

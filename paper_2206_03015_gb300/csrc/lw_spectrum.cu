@@ -141,12 +141,15 @@ __global__ void spectrum_direct_kernel(RecReader<T> rd, int64_t n_pix, int N, in
 
 // ---------------------------------------------------------------- four-step
 
-// Pass 1: tile of N1 rows x CT columns (columns j2 in [c0, c0+CT)) of sequence seq.
-template <typename T, int CT>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N1, int logN1,
-                                      int N2, T scale, const typename V2<T>::type* __restrict__ tw,
-                                      typename V2<T>::type* __restrict__ Y, int64_t seq0) {
+// Pass 1: tile of N1 = 2^LOGN1 rows x CT columns (columns j2 in [c0, c0+CT)) of sequence
+// seq.
+template <typename T, int CT, int LOGN1>
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
+    spectrum_pass1_kernel(RecReader<T> rd, int64_t n_pix, int N, int N2, T scale,
+                          const typename V2<T>::type* __restrict__ tw,
+                          typename V2<T>::type* __restrict__ Y, int64_t seq0) {
     using C = typename V2<T>::type;
+    constexpr int N1 = 1 << LOGN1, logN1 = LOGN1;
     extern __shared__ unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);   // [N1][CT]
     C* wrow = buf + N1 * CT;                    // [N1]
@@ -156,11 +159,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_ke
     // loads in batches of kBatch elements per thread, all in flight before any is converted
     constexpr int kBatch = 8;
     using Raw = typename RecReader<T>::Raw;
-    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * blockDim.x) {
+    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * kFftThreads) {
         Raw va[kBatch], vb[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int t = t0 + u * blockDim.x + threadIdx.x;
+            const int t = t0 + u * kFftThreads + threadIdx.x;
             const int64_t j = (int64_t)(t / CT) * N2 + c0 + t % CT;
             const bool in = t < N1 * CT;
             va[u] = in && sr.ra >= 0 ? rd.load(sr.ra, N, j) : Raw{};
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_ke
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int t = t0 + u * blockDim.x + threadIdx.x;
+            const int t = t0 + u * kFftThreads + threadIdx.x;
             if (t < N1 * CT) {
                 C z;
                 z.x = (scale * rd.cvt_fp64(va[u])) * scale;
@@ -178,23 +181,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_ke
         }
     }
     // first twiddle factor tw[c0 l1] of each row, shared by the tile's CT columns
-    for (int l1 = threadIdx.x; l1 < N1; l1 += blockDim.x)
+    for (int l1 = threadIdx.x; l1 < N1; l1 += kFftThreads)
         wrow[l1] = tw[((int64_t)c0 * l1) & (N - 1)];
     __syncthreads();
-    fft_smem<C, CT, false>(buf, N1, logN1, tw, N);
+    fft_smem_fixed<C, CT, false, LOGN1>(buf, tw, N);
     C* Ys = Y + seq * (int64_t)N;
     // twiddle exp(2 pi i j2 l1 / N), j2 = c0 + c, as tw[c0 l1] tw[c l1]: the second factor
     // lies in the table's first CT * N1 entries, which stay in cache
-    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * blockDim.x) {
+    for (int t0 = 0; t0 < N1 * CT; t0 += kBatch * kFftThreads) {
         C w2[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int t = t0 + u * blockDim.x + threadIdx.x;
+            const int t = t0 + u * kFftThreads + threadIdx.x;
             w2[u] = t < N1 * CT ? tw[(t % CT) * (t / CT)] : C{};
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int t = t0 + u * blockDim.x + threadIdx.x;
+            const int t = t0 + u * kFftThreads + threadIdx.x;
             if (t < N1 * CT) {
                 const int c = t % CT, l1 = t / CT;
                 __stcs(Ys + (int64_t)l1 * N2 + c0 + c, cmul(buf[l1 * CT + c], cmul(wrow[l1], w2[u])));
@@ -207,17 +210,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) spectrum_pass1_ke
 // mirrors N1 - l1 of the three sequences of one pixel pair, transformed together (6 *
 // ROWS interleaved sequences); each spectrum value is written once (no atomics, no
 // zeroing): every l <= N/2 has row l mod N1, which one CTA holds as l1 or as a mirror.
-template <typename T, int ROWS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
-    spectrum_pass2_kernel(int64_t n_pix, int N, int N1, int N2, int logN2,
+template <typename T, int ROWS, int LOGN2>
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
+    spectrum_pass2_kernel(int64_t n_pix, int N, int N1,
                           const typename V2<T>::type* __restrict__ tw,
                           const typename V2<T>::type* __restrict__ Y, T* __restrict__ S,
                           typename V2<T>::type* __restrict__ X, int64_t pair0) {
     using C = typename V2<T>::type;
     constexpr int Cn = 6 * ROWS;   // column = (r*3 + kind)*2 + side
+    constexpr int N2 = 1 << LOGN2, logN2 = LOGN2;
+    constexpr int sh = LOGN2 > 5 ? LOGN2 - 5 : 0;
     extern __shared__ unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);   // [N2][Cn], padded (fft_slot)
-    const int sh = fft_pad_shift(logN2);
     const int64_t pair = pair0 + blockIdx.y;
     const int r0 = blockIdx.x * ROWS;
     const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     // cp.async, all of them in flight at once; rows past N1/2 are zero-filled
     const C* Yp = Y + pair * 3 * (int64_t)N;
 #pragma unroll 1
-    for (int t = threadIdx.x; t < Cn * N2; t += blockDim.x) {
+    for (int t = threadIdx.x; t < Cn * N2; t += kFftThreads) {
         const int j2 = t & (N2 - 1), col = t >> logN2;
         const int side = col & 1, kind = (col >> 1) % 3, r = col / 6;
         const int l1 = r0 + r;
@@ -242,12 +246,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<C, Cn, true>(buf, N2, logN2, tw, N, sh);
+    fft_smem_fixed<C, Cn, true, LOGN2>(buf, tw, N);
     const int64_t nl = N / 2 + 1;
     const int half = N / 2;
     T* S0 = S + m0 * nl;
     T* S1 = S + m1 * nl;
-    for (int t = threadIdx.x; t < 2 * ROWS * N2; t += blockDim.x) {
+    for (int t = threadIdx.x; t < 2 * ROWS * N2; t += kFftThreads) {
         const int r = t % ROWS, side = (t / ROWS) & 1, l2 = t / (2 * ROWS);
         const int l1 = r0 + r;
         if (l1 > N1 / 2) continue;
@@ -360,19 +364,24 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     const int logN2 = (logN + 1) / 2, logN1 = logN - logN2;
     const int N1 = 1 << logN1, N2 = 1 << logN2;
     constexpr int CT = 16;
+    // logN in 13..18: logN1 and logN2 in 6..9
+    const int lsel1 = logN1 - 6, lsel2 = logN2 - 6;
+    if (lsel1 < 0 || lsel1 > 3 || lsel2 < 0 || lsel2 > 3) return LW_EUNSUPPORTED;
     {
+        using K1 = void (*)(RecReader<T>, int64_t, int, int, T, const C*, C*, int64_t);
+        const K1 k1s[4] = {spectrum_pass1_kernel<T, CT, 6>, spectrum_pass1_kernel<T, CT, 7>,
+                           spectrum_pass1_kernel<T, CT, 8>, spectrum_pass1_kernel<T, CT, 9>};
+        const K1 kern = k1s[lsel1];
         const size_t smem = sizeof(C) * (size_t)N1 * (CT + 1);
         if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(spectrum_pass1_kernel<T, CT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return LW_ECUDA;
         // grid y is limited to 65535: sequences in chunks of 21845 pixel pairs
         for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
             const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
             dim3 grid((unsigned)(N2 / CT), (unsigned)(3 * np));
-            spectrum_pass1_kernel<T, CT><<<grid, 256, smem, st>>>(rd, n_pix, (int)N, N1, logN1,
-                                                                  N2, scale, tw, Y, 3 * p0);
+            kern<<<grid, kFftThreads, smem, st>>>(rd, n_pix, (int)N, N2, scale, tw, Y, 3 * p0);
             if (launch_status() != LW_OK) return LW_ECUDA;
         }
     }
@@ -382,8 +391,15 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
         while (rows > 1 && sizeof(C) * (size_t)fft_slots(N2, logN2, 6 * rows) > 96 * 1024)
             rows >>= 1;
         const size_t smem = sizeof(C) * (size_t)fft_slots(N2, logN2, 6 * rows);
-        auto kern = rows == 4 ? spectrum_pass2_kernel<T, 4>
-                    : rows == 2 ? spectrum_pass2_kernel<T, 2> : spectrum_pass2_kernel<T, 1>;
+        using K2 = void (*)(int64_t, int, int, const C*, const C*, T*, C*, int64_t);
+        const K2 k2s[3][4] = {
+            {spectrum_pass2_kernel<T, 1, 6>, spectrum_pass2_kernel<T, 1, 7>,
+             spectrum_pass2_kernel<T, 1, 8>, spectrum_pass2_kernel<T, 1, 9>},
+            {spectrum_pass2_kernel<T, 2, 6>, spectrum_pass2_kernel<T, 2, 7>,
+             spectrum_pass2_kernel<T, 2, 8>, spectrum_pass2_kernel<T, 2, 9>},
+            {spectrum_pass2_kernel<T, 4, 6>, spectrum_pass2_kernel<T, 4, 7>,
+             spectrum_pass2_kernel<T, 4, 8>, spectrum_pass2_kernel<T, 4, 9>}};
+        const K2 kern = k2s[rows == 4 ? 2 : rows == 2 ? 1 : 0][lsel2];
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
@@ -392,7 +408,7 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
         for (int64_t p0 = 0; p0 < n_pairs; p0 += kPairsPerLaunch) {
             const int64_t np = std::min<int64_t>(kPairsPerLaunch, n_pairs - p0);
             dim3 grid((unsigned)groups, (unsigned)np);
-            kern<<<grid, 256, smem, st>>>(n_pix, (int)N, N1, N2, logN2, tw, Y, S, X, p0);
+            kern<<<grid, kFftThreads, smem, st>>>(n_pix, (int)N, N1, tw, Y, S, X, p0);
             if (launch_status() != LW_OK) return LW_ECUDA;
         }
         return LW_OK;
