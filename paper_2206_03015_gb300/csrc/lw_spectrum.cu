@@ -227,21 +227,34 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
     const int64_t m0 = 2 * pair, m1 = 2 * pair + 1;
     const bool has1 = m1 < n_pix;
     // every element of the tile is copied straight into its bit-reversed slot by
-    // cp.async, all of them in flight at once; rows past N1/2 are zero-filled
+    // cp.async, all of them in flight at once; rows past N1/2 are zero-filled. A thread
+    // keeps its j2 values (TPC threads per column, CPI columns per round) so that the
+    // bit-reversed slot offsets are computed once; a round's column is decoded once.
+    constexpr int TPC = N2 < kFftThreads ? N2 : kFftThreads;
+    constexpr int CPI = kFftThreads / TPC;
+    constexpr int JPT = N2 / TPC;
     const C* Yp = Y + pair * 3 * (int64_t)N;
+    int jslot[JPT];
+#pragma unroll
+    for (int u = 0; u < JPT; ++u) {
+        const int jr = bitrev(threadIdx.x % TPC + u * TPC, logN2);
+        jslot[u] = jr * Cn + (jr >> sh);
+    }
 #pragma unroll 1
-    for (int t = threadIdx.x; t < Cn * N2; t += kFftThreads) {
-        const int j2 = t & (N2 - 1), col = t >> logN2;
+    for (int col = threadIdx.x / TPC; col < Cn; col += CPI) {
         const int side = col & 1, kind = (col >> 1) % 3, r = col / 6;
         const int l1 = r0 + r;
         const bool valid = l1 <= N1 / 2;
         const int row = valid ? (side ? (N1 - l1) & (N1 - 1) : l1) : 0;
-        const C* src = Yp + (kind * N + row * N2 + j2);
-        C* dst = buf + fft_slot<Cn, true>(bitrev(j2, logN2), col, sh);
-        if (sizeof(C) == 8)
-            cp_async8_zfill(dst, src, valid);
-        else
-            cp_async16_zfill(dst, src, valid);
+        const C* src = Yp + (kind * N + row * N2 + threadIdx.x % TPC);
+#pragma unroll
+        for (int u = 0; u < JPT; ++u) {
+            C* dst = buf + (jslot[u] + col);
+            if (sizeof(C) == 8)
+                cp_async8_zfill(dst, src + u * TPC, valid);
+            else
+                cp_async16_zfill(dst, src + u * TPC, valid);
+        }
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -249,25 +262,31 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
     fft_smem_fixed<C, Cn, true, LOGN2>(buf, tw, N);
     const int64_t nl = N / 2 + 1;
     const int half = N / 2;
+    // split: thread t takes row r = t % ROWS of side (t / ROWS) % 2 for every
+    // (2 ROWS)-th l2; both are fixed per thread since kFftThreads is a multiple of 2 ROWS
+    constexpr int L2STEP = kFftThreads / (2 * ROWS);
+    const int r = threadIdx.x % ROWS, side = (threadIdx.x / ROWS) & 1;
+    const int l1 = r0 + r;
+    if (l1 > N1 / 2) return;
+    const int l1p = (N1 - l1) & (N1 - 1);
+    if (side == 1 && l1p == l1) return;                 // self-mirrored row: once
+    const int row = side ? l1p : l1;
     T* S0 = S + m0 * nl;
     T* S1 = S + m1 * nl;
-    for (int t = threadIdx.x; t < 2 * ROWS * N2; t += kFftThreads) {
-        const int r = t % ROWS, side = (t / ROWS) & 1, l2 = t / (2 * ROWS);
-        const int l1 = r0 + r;
-        if (l1 > N1 / 2) continue;
-        const int l1p = (N1 - l1) & (N1 - 1);
-        if (side == 1 && l1p == l1) continue;          // self-mirrored row: once
-        const int row = side ? l1p : l1;
+    const C* bz = buf + (r * 6 + side);        // column (r*3 + kind)*2 + side, kind 0
+    const C* bm = buf + (r * 6 + 1 - side);    // the other side's column
+#pragma unroll 2
+    for (int l2 = threadIdx.x / (2 * ROWS); l2 < N2; l2 += L2STEP) {
         const int l = row + N1 * l2;
-        if (l > half) continue;
+        if (l > half) break;   // l grows with l2
         // mirror index N - l lives in the other side's column
         const int l2m = row == 0 ? (N2 - l2) & (N2 - 1) : N2 - 1 - l2;
+        const int ol = l2 * Cn + (l2 >> sh), om = l2m * Cn + (l2m >> sh);
         T pw0 = (T)0, pw1 = (T)0;
 #pragma unroll
         for (int kind = 0; kind < 3; ++kind) {
-            const int col = (r * 3 + kind) * 2;
-            const C zl = buf[fft_slot<Cn, true>(l2, col + side, sh)];
-            const C zn = buf[fft_slot<Cn, true>(l2m, col + (1 - side), sh)];
+            const C zl = bz[ol + 2 * kind];
+            const C zn = bm[om + 2 * kind];
             C A, B;   // spectra of the two real rows of the sequence
             A.x = (T)0.5 * (zl.x + zn.x);
             A.y = (T)0.5 * (zl.y - zn.y);
