@@ -180,10 +180,12 @@ def run_ours(args, rank, world, dist):
     bnd = lw.lw_grid_bounds(traj0, det).cpu().numpy()
     grid = lw.grid_from_bounds(bnd[0], bnd[1], w.n_bins)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
+    # the timed mixed path: FP32 record (LW_MIXED_F32) by default, FP64 record with --mixed f64
+    MIX = lw.LW_MIXED_F32 if args.mixed == "f32" else lw.LW_MIXED
+    shp, dt = lw.record_shape(det, grid, MIX)
     rec_m = torch.empty(shp, dtype=dt, device=dev)
     S_m = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float32, device=dev)
-    ws_s = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_MIXED, det.n_pix, grid), dev)
+    ws_s = lw.workspace(lw.spectrum_workspace_bytes(MIX, det.n_pix, grid), dev)
     ws_t = traj0.ws
     ev_dep = []
 
@@ -194,11 +196,11 @@ def run_ours(args, rank, world, dist):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-        lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED, record=rec_m, status=status)
+        lw.lw_deposit_time_domain(traj, det, grid, MIX, record=rec_m, status=status)
         if timed:
             e1.record()
             ev_dep.append((e0, e1))
-        lw.lw_spectrum(rec_m, lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S_m)
+        lw.lw_spectrum(rec_m, MIX, det.n_pix, grid, ws=ws_s, out=S_m)
 
     def barrier():
         if dist is not None:
@@ -246,6 +248,8 @@ def run_ours(args, rank, world, dist):
                    f"{args.n_s} steps x {args.nx}x{args.nx} px, {args.n_bins} bins",
                    "n_e": tr.n_e, "n_s": tr.n_s, "n_pix": w.n_pix, "n_bins": w.n_bins,
                    "deposits_per_step_per_gpu": n_dep, "block": args.block,
+                   "precision": ("LW_MIXED_F32 (FP32 record)" if MIX == lw.LW_MIXED_F32
+                                 else "LW_MIXED (FP64 record)"),
                    "l2": "inputs larger than L2 (mixed trajectory section %.1f GB)"
                          % (traj0.ws.numel() / 1e9),
                    "parallelism": f"detector-sharded x{world} (one detector per GPU)",
@@ -265,7 +269,7 @@ def run_ours(args, rank, world, dist):
     ns1 = tr.n_s + 1
     n_blocks = -(-ns1 // args.block)
     traj_bytes = tr.n_e * (ns1 * (16 + 24) + n_blocks * 32)
-    rec_bytes = w.n_pix * 3 * w.n_bins * 8
+    rec_bytes = w.n_pix * 3 * w.n_bins * rec_m.element_size()
     alg_bytes = traj_bytes + rec_bytes
     achieved = alg_bytes / (dep_ms * 1e-3) / 1e9
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2206_03015_gb300", "csrc",
@@ -279,6 +283,23 @@ def run_ours(args, rank, world, dist):
                           "grid_points": n_points,
                           "atomics_per_s": 3.0 * n_points / (dep_ms * 1e-3)}
     result["clocks"] = clocks
+    # the other mixed record beside it (FP64 record when the FP32 one is timed)
+    if MIX == lw.LW_MIXED_F32:
+        rec_64 = torch.empty(lw.record_shape(det, grid, lw.LW_MIXED)[0], dtype=torch.float64,
+                             device=dev)
+        S_64m = torch.empty_like(S_m)
+
+        def step_mixed64(timed=False):
+            traj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_MIXED,
+                                             block=args.block, device=dev, ws=ws_t)
+            lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED, record=rec_64,
+                                      status=status)
+            lw.lw_spectrum(rec_64, lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S_64m)
+
+        ms_64m, _ = timed_loop(step_mixed64, args.steps, args.warmup)
+        result["mixed_fp64_record"] = {"ms_per_step": ms_64m / args.steps,
+                                       "value": n_dep * world / (ms_64m / args.steps * 1e-3)}
+        del rec_64, S_64m
     torch.cuda.synchronize()
     st_m = int(status.item())
 
@@ -357,13 +378,13 @@ def run_ours(args, rank, world, dist):
                     if c == 0:
                         rec2[b].zero_()   # the spectrum two steps back (same stream) is done
                     s_dp.wait_event(ev_pr[q])
-                    lw.lw_deposit_time_domain(tj, det, grid, lw.LW_MIXED, record=rec2[b],
+                    lw.lw_deposit_time_domain(tj, det, grid, MIX, record=rec2[b],
                                               accumulate=True, status=status)
                     ev_dp[q].record(s_dp)
             with torch.cuda.stream(s_dp):
                 if not first_b:
                     s_dp.wait_event(ev_bk[b])              # read-back two steps back is done
-                lw.lw_spectrum(rec2[b], lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S2[b])
+                lw.lw_spectrum(rec2[b], MIX, det.n_pix, grid, ws=ws_s, out=S2[b])
                 ev_sp[b].record(s_dp)
             with torch.cuda.stream(s_bk):
                 s_bk.wait_event(ev_sp[b])
@@ -622,6 +643,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mixed", default="f32", choices=["f32", "f64"],
+                    help="record of the timed mixed path: FP32 (LW_MIXED_F32) or FP64 (LW_MIXED)")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -61,8 +61,13 @@ enum {
     LW_MIXED = 1,  /* FP64-exact bin coordinates carried as integer + FP32 fraction, FP32
                       field and interpolation, contributions added to an FP64 record by
                       the L2 (red.global.add.f64), FP32 FFT */
-    LW_MIXED_KAHAN = 2  /* as LW_MIXED but the record is a compensated FP32 pair
+    LW_MIXED_KAHAN = 2, /* as LW_MIXED but the record is a compensated FP32 pair
                            (sum, compensation): atomic add with return + two-sum */
+    LW_MIXED_F32 = 3    /* as LW_MIXED but the record is FP32, added to by the L2
+                           (red.global.add.f32): half the record's bytes and faster
+                           atomics; each bin's sum carries FP32 rounding, so it suits
+                           records whose bins collect few contributions each (about 3 on
+                           the C2 workload; the error grows with the count) */
 };
 
 /* Field terms (bit mask) of lw_deposit_time_domain. */
@@ -187,12 +192,14 @@ int lw_grid_bounds(const lw_traj* traj, const lw_detector* det, double* bounds, 
  * LW_FP64), the field in FP32 from the stable form
  *   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
  *   F = [(n - beta)(n . beta_dot) - D beta_dot] / D^3,
- * and accumulates into FP64 (LW_MIXED) or compensated FP32 pairs (LW_MIXED_KAHAN).
- *   precision    LW_FP64, LW_MIXED or LW_MIXED_KAHAN (the matching section must exist)
+ * and accumulates into FP64 (LW_MIXED), compensated FP32 pairs (LW_MIXED_KAHAN)
+ * or FP32 (LW_MIXED_F32).
+ *   precision    LW_FP64, LW_MIXED, LW_MIXED_KAHAN or LW_MIXED_F32 (the matching
+ *                section must exist)
  *   field_flags  LW_FIELD_* mask (non-zero)
- *   record       device, 8 bytes per value; LW_FP64 and LW_MIXED: double
- *                [n_pix][3][n_bins]; LW_MIXED_KAHAN: float2 [n_pix][3][n_bins] =
- *                (sum, compensation), value = sum + compensation
+ *   record       device; LW_FP64 and LW_MIXED: double [n_pix][3][n_bins];
+ *                LW_MIXED_KAHAN: float2 [n_pix][3][n_bins] = (sum, compensation),
+ *                value = sum + compensation; LW_MIXED_F32: float [n_pix][3][n_bins]
  *   accumulate   0: the record is zeroed first; 1: add to its contents
  *   status       device int32, OR-ed with LW_ST_* bits (may be NULL)
  * Grid points outside [0, n_bins) are skipped (LW_ST_CLIP).
@@ -210,9 +217,9 @@ int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* det, const lw
  *   record    device, layout of lw_deposit_time_domain for `precision`
  *   n_pix     pixels in the record
  *   q         particle charge [C]
- *   spectrum  device; LW_FP64: double, LW_MIXED(_KAHAN): float [n_pix][n_bins/2+1]
+ *   spectrum  device; LW_FP64: double, the LW_MIXED* modes: float [n_pix][n_bins/2+1]
  *   X_save    device or NULL; receives X' = sqrt(K) dt_u X (so that S = sum_c |X'_c|^2),
- *             K = q^2/(16 pi^3 eps0 c0), as LW_FP64: double2, LW_MIXED(_KAHAN): float2
+ *             K = q^2/(16 pi^3 eps0 c0), as LW_FP64: double2, the LW_MIXED* modes: float2
  *             [n_pix][3][n_bins/2+1]
  *   ws        device scratch for the two-pass FFT (n_bins above 4096); NULL = query
  *   ws_bytes  in: size of ws; out: bytes required (0 when none is needed)
@@ -291,7 +298,7 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
 
 /* Several independent problems ("variants": own trajectories, detector, grid
  * and record) deposited by one persistent launch of the mixed-precision
- * deposit (LW_MIXED or LW_MIXED_KAHAN).  The work is cut into units of
+ * deposit (LW_MIXED, LW_MIXED_KAHAN or LW_MIXED_F32).  The work is cut into units of
  * (variant, 512-pixel tile, chunk of electrons) that resident CTAs take from a
  * list: variants largest first, each variant's chunks in arrival order (the
  * upload's electron order) with its tiles fastest, so variants of very

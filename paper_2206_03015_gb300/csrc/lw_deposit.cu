@@ -288,13 +288,23 @@ constexpr int kJobTable = 128;
 // on average (at most 5); alternating interpolation and bisection needed 3.2.
 constexpr int kFalsiProbes = 8;
 
-template <bool KAHAN>
+// Record accumulation of the mixed modes: FP64 (red.global.add.f64), compensated FP32
+// pair, or FP32 (red.global.add.f32).
+enum { kAccF64 = 0, kAccKahan = 1, kAccF32 = 2 };
+
+template <int ACC>
 __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
-    if (KAHAN) {
+    if (ACC == kAccKahan) {
         kahan_atomic_add(static_cast<float2*>(rec) + idx, v);
+    } else if (ACC == kAccF32) {
+        atomicAdd(static_cast<float*>(rec) + idx, v);
     } else {
-        atomicAdd(static_cast<double*>(rec) + idx, (double)v);   // red.global.add.f64
+        atomicAdd(static_cast<double*>(rec) + idx, (double)v);
     }
+}
+
+__host__ __device__ constexpr size_t record_elem_bytes(int precision) {
+    return precision == LW_MIXED_F32 ? 4 : 8;   // float, or double / float2
 }
 
 // FP64 bin index of a trajectory end sample, with the FP64 path's operation order.
@@ -348,7 +358,7 @@ __host__ __device__ constexpr size_t stage_bytes(int B) {
 // point per lane and round), each lane finding its step, evaluating the two
 // fields and adding the interpolated value.  Blocks are staged into two
 // alternating shared buffers by asynchronous copies, one block ahead.
-template <int PIX, bool KAHAN>
+template <int PIX, int ACC>
 __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     constexpr int kSlots = kMixThreads * PIX;
@@ -535,9 +545,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 const float wb = du > 0.0f ? a0 * __frcp_rn(du) : 0.0f;
                 const float wa = 1.0f - wb;
                 const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
-                accumulate<KAHAN>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
-                accumulate<KAHAN>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-                accumulate<KAHAN>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+                accumulate<ACC>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
+                accumulate<ACC>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
+                accumulate<ACC>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
             };
             // a job handed to the warp: the slot's block data from shared memory
             auto job = [&](int sl, int j) {
@@ -891,9 +901,9 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
     block_status_or(p.status, bits);
 }
 
-template <int PIX, bool KAHAN>
+template <int PIX, int ACC>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
-    const int bits = mixed_cta<PIX, KAHAN>(p, blockIdx.x, blockIdx.y);
+    const int bits = mixed_cta<PIX, ACC>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
 }
 
@@ -912,7 +922,7 @@ struct BatchUnit {
 constexpr int kBatchMaxItems = 256;
 __constant__ DepositArgs c_batch_vars[kBatchMaxItems];
 
-template <int PIX, bool KAHAN>
+template <int PIX, int ACC>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     deposit_batched_kernel(const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
@@ -923,7 +933,7 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
         if (u >= n_units) break;
         const BatchUnit un = units[u];
         const DepositArgs& p = c_batch_vars[un.variant];
-        const int bits = mixed_cta<PIX, KAHAN>(p, un.tile, un.chunk);
+        const int bits = mixed_cta<PIX, ACC>(p, un.tile, un.chunk);
         block_status_or(p.status, bits);
     }
 }
@@ -931,18 +941,18 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
 // Zeroes every variant's record (n_pix * 3 * n_bins values of 8 bytes): grid y =
 // variant, x = CTAs striding over it, with 16-byte stores where the record is
 // 16-byte aligned (an odd last value is stored alone).
-__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars) {
+__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int elem_bytes) {
     const DepositArgs& a = vars[blockIdx.y];
-    const int64_t n = a.n_pix * 3 * a.n_bins;
+    const int64_t n = a.n_pix * 3 * a.n_bins * (elem_bytes / 4);   // 4-byte words
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float* rec = static_cast<float*>(a.record);
     if ((reinterpret_cast<uintptr_t>(a.record) & 15) == 0) {
-        float4* rec = static_cast<float4*>(a.record);
-        for (int64_t i = i0; i < n / 2; i += stride) rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((n & 1) && i0 == 0) static_cast<double*>(a.record)[n - 1] = 0.0;
+        float4* rec4 = static_cast<float4*>(a.record);
+        for (int64_t i = i0; i < n / 4; i += stride) rec4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = (n / 4) * 4 + i0; i < n; i += stride) rec[i] = 0.0f;
     } else {
-        double* rec = static_cast<double*>(a.record);
-        for (int64_t i = i0; i < n; i += stride) rec[i] = 0.0;
+        for (int64_t i = i0; i < n; i += stride) rec[i] = 0.0f;
     }
 }
 
@@ -960,12 +970,13 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     if (!(grid->dt_u > 0.0) || !isfinite(grid->dt_u) || !isfinite(grid->t_min)) return LW_EINVAL;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     if ((field_flags & LW_FIELD_VELOCITY) && !(det->R > 0.0)) return LW_EINVAL;
-    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
+        precision != LW_MIXED_F32)
         return LW_EINVAL;
     if (precision == LW_FP64 && !(traj->sections & LW_SECTION_FP64)) return LW_EINVAL;
     if (precision != LW_FP64 && !(traj->sections & LW_SECTION_MIXED)) return LW_EINVAL;
     cudaStream_t st = as_stream(stream);
-    const size_t elem = 8;   // double, or a (sum, compensation) float pair
+    const size_t elem = record_elem_bytes(precision);
     if (!accumulate &&
         cudaMemsetAsync(record, 0, elem * 3 * (size_t)(det->n_pix * grid->n_bins), st) !=
             cudaSuccess)
@@ -1014,8 +1025,9 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
     const size_t smem = 2 * stage_bytes(traj->block);   // double-buffered staging
     // static tables + double-buffered staging exceed the 48 KB default: opt in
-    auto kern = precision == LW_MIXED_KAHAN ? deposit_mixed_kernel<PIX, true>
-                                            : deposit_mixed_kernel<PIX, false>;
+    auto kern = precision == LW_MIXED_KAHAN ? deposit_mixed_kernel<PIX, kAccKahan>
+                : precision == LW_MIXED_F32 ? deposit_mixed_kernel<PIX, kAccF32>
+                                            : deposit_mixed_kernel<PIX, kAccF64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return LW_ECUDA;
@@ -1053,7 +1065,8 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
     constexpr int PIX = kMixPix;
     if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
     if (n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
-    if (precision != LW_MIXED && precision != LW_MIXED_KAHAN) return LW_EUNSUPPORTED;
+    if (precision != LW_MIXED && precision != LW_MIXED_KAHAN && precision != LW_MIXED_F32)
+        return LW_EUNSUPPORTED;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     std::vector<DepositArgs> vars((size_t)n_items);
     std::vector<BatchUnit> units;
@@ -1174,14 +1187,16 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     const DepositArgs* vars = reinterpret_cast<const DepositArgs*>(base + plan->offsets[1]);
     const BatchUnit* units = reinterpret_cast<const BatchUnit*>(base + plan->offsets[2]);
     if (plan->n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
-    zero_records_kernel<<<dim3(kSms * 4, (unsigned)plan->n_items), 256, 0, st>>>(vars);
+    zero_records_kernel<<<dim3(kSms * 4, (unsigned)plan->n_items), 256, 0, st>>>(
+        vars, (int)record_elem_bytes(plan->precision));
     if (launch_status() != LW_OK) return LW_ECUDA;
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return LW_ECUDA;
     if (cudaMemcpyToSymbolAsync(c_batch_vars, vars, sizeof(DepositArgs) * (size_t)plan->n_items,
                                 0, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return LW_ECUDA;
-    auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, true>
-                                                  : deposit_batched_kernel<PIX, false>;
+    auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, kAccKahan>
+                : plan->precision == LW_MIXED_F32 ? deposit_batched_kernel<PIX, kAccF32>
+                                                  : deposit_batched_kernel<PIX, kAccF64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              plan->smem_bytes) != cudaSuccess)
         return LW_ECUDA;

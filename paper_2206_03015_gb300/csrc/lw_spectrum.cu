@@ -26,6 +26,9 @@
 namespace lw {
 namespace {
 
+// Record formats of the mixed modes.
+enum { kRecF64 = 0, kRecKahan = 1, kRecF32 = 2 };
+
 // Record readers.  load() fetches an element's raw bits, cvt() turns them into T; pass 1
 // issues a batch of loads before it converts any, so that they are all in flight.
 template <typename T> struct RecReader;
@@ -40,21 +43,26 @@ template <> struct RecReader<double> {
     }
 };
 template <> struct RecReader<float> {
-    using Raw = uint2;   // a double, or a (sum, compensation) float pair
+    using Raw = uint2;   // a double, a (sum, compensation) float pair, or a float in .x
     const void* rec;
-    int kahan;   // 1: (sum, compensation) float pairs, 0: double
+    int kind;   // kRecF64 double, kRecKahan (sum, compensation) pairs, kRecF32 float
     __device__ uint2 load(int64_t row, int64_t N, int64_t j) const {
+        if (kind == kRecF32)
+            return make_uint2(__float_as_uint(__ldcs(static_cast<const float*>(rec) + row * N + j)),
+                              0u);
         return __ldcs(static_cast<const uint2*>(rec) + row * N + j);
     }
     __device__ float cvt(uint2 v) const {   // double -> float on the integer pipe
-        if (kahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
+        if (kind == kRecF32) return __uint_as_float(v.x);
+        if (kind == kRecKahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
         return to_float_bits(v.y, v.x);   // little-endian double: v.y holds the high word
     }
     // the same rounding by the FP64 pipe's conversion: pass 1 converts one row of each
     // pair this way and one on the integer pipe, which its index work already loads
     // (results differ only below the smallest normal float, which this one keeps)
     __device__ float cvt_fp64(uint2 v) const {
-        if (kahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
+        if (kind == kRecF32) return __uint_as_float(v.x);
+        if (kind == kRecKahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
         return __double2float_rn(__hiloint2double((int)v.y, (int)v.x));
     }
     __device__ float operator()(int64_t row, int64_t N, int64_t j) const {
@@ -320,19 +328,19 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
     }
 }
 
-template <typename T> void set_reader(RecReader<T>& rd, const void* rec, int kahan);
+template <typename T> void set_reader(RecReader<T>& rd, const void* rec, int kind);
 template <> void set_reader<double>(RecReader<double>& rd, const void* rec, int) {
     rd.rec = static_cast<const double*>(rec);
 }
-template <> void set_reader<float>(RecReader<float>& rd, const void* rec, int kahan) {
+template <> void set_reader<float>(RecReader<float>& rd, const void* rec, int kind) {
     rd.rec = rec;
-    rd.kahan = kahan;
+    rd.kind = kind;
 }
 
 constexpr int64_t kPairsPerLaunch = 21845;   // 3 x pairs <= 65535 (grid y limit)
 
 template <typename T>
-int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g, double q,
+int run_spectrum(const void* record, int kind, int64_t n_pix, const lw_grid* g, double q,
                  void* spectrum, void* X_save, void* ws, size_t* ws_bytes, cudaStream_t st) {
     using C = typename V2<T>::type;
     const int64_t N = g->n_bins;
@@ -359,7 +367,7 @@ int run_spectrum(const void* record, int kahan, int64_t n_pix, const lw_grid* g,
     // normal FP32 range: X' = sqrt(K) dt_u X and S = |X'|^2
     const T scale = (T)sqrt(sqrt(K) * g->dt_u);
     RecReader<T> rd;
-    set_reader<T>(rd, record, kahan);
+    set_reader<T>(rd, record, kind);
     T* S = static_cast<T*>(spectrum);
     C* X = static_cast<C*>(X_save);
     const int nl = (int)(N / 2 + 1);
@@ -443,7 +451,8 @@ extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
                            const lw_grid* grid, double q, void* spectrum, void* X_save, void* ws,
                            size_t* ws_bytes, void* stream) {
     if (!grid || !ws_bytes || n_pix < 1) return LW_EINVAL;
-    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
+        precision != LW_MIXED_F32)
         return LW_EINVAL;
     const int64_t N = grid->n_bins;
     if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;
@@ -453,8 +462,10 @@ extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
     if (precision == LW_FP64)
         return run_spectrum<double>(record, 0, n_pix, grid, q, spectrum, X_save, ws, ws_bytes,
                                     st);
-    return run_spectrum<float>(record, precision == LW_MIXED_KAHAN, n_pix, grid, q, spectrum,
-                               X_save, ws, ws_bytes, st);
+    const int kind = precision == LW_MIXED_KAHAN ? kRecKahan
+                     : precision == LW_MIXED_F32 ? kRecF32 : kRecF64;
+    return run_spectrum<float>(record, kind, n_pix, grid, q, spectrum, X_save, ws, ws_bytes,
+                               st);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,7 +507,8 @@ extern "C" int lw_spectrum_static(const void* record, int32_t precision, int64_t
                                   const lw_grid* grid, double q, void* spectrum, void* X_save,
                                   void* stream) {
     if (!grid || n_pix < 1 || !record || !spectrum) return LW_EINVAL;
-    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN)
+    if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
+        precision != LW_MIXED_F32)
         return LW_EINVAL;
     const int64_t N = grid->n_bins;
     if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;

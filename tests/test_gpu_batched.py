@@ -31,24 +31,26 @@ def variants():
     return out
 
 
-def _records(variants):
+def _records(variants, precision=lw.LW_MIXED):
     recs = []
     for (_, _, _, det, grid) in variants:
-        shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
+        shp, dt = lw.record_shape(det, grid, precision)
         recs.append(torch.empty(shp, dtype=dt, device="cuda"))
     return recs
 
 
-def test_batched_equals_per_variant(variants):
-    recs = _records(variants)
+@pytest.mark.parametrize("precision,tol", [(lw.LW_MIXED, 1e-12), (lw.LW_MIXED_F32, 1e-6)])
+def test_batched_equals_per_variant(variants, precision, tol):
+    recs = _records(variants, precision)
     bp = lw.lw_batch_plan([v[2] for v in variants], [v[3] for v in variants],
-                          [v[4] for v in variants], recs)
+                          [v[4] for v in variants], recs, precision=precision)
     assert bp.plan.n_units >= len(variants)
     lw.lw_batch_deposit(bp)
     for (w, _, traj, det, grid), rec in zip(variants, recs):
-        ref = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED)
+        ref = lw.lw_deposit_time_domain(traj, det, grid, precision)
         torch.cuda.synchronize()
-        assert rel_l2(rec.cpu().numpy(), ref.cpu().numpy()) <= 1e-12, w.name
+        # FP32 records: the same contributions, added in another order
+        assert rel_l2(rec.double().cpu().numpy(), ref.double().cpu().numpy()) <= tol, w.name
 
 
 def test_autotuned_batch_matches_oracle_on_sampled_variants(variants):

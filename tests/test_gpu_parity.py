@@ -100,7 +100,7 @@ def test_fp64_record_and_spectrum(name):
 
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("block", [16, 128, 1024])
-@pytest.mark.parametrize("precision", [lw.LW_MIXED, lw.LW_MIXED_KAHAN])
+@pytest.mark.parametrize("precision", [lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32])
 def test_mixed_record_and_spectrum(name, block, precision):
     tr, n_hat, grid, flags, R = _case(name)
     g = gpu_run(tr, n_hat, grid, precision, flags, R, block=block)
@@ -135,6 +135,9 @@ def test_spectrum_matches_oracle(n_bins, n_pix):
     assert rel_l2(S_k.double().cpu().numpy(), S_o) <= 1e-5
     S_m = lw.lw_spectrum(torch.from_numpy(rec).cuda(), lw.LW_MIXED, n_pix, grid)
     assert rel_l2(S_m.double().cpu().numpy(), S_o) <= 1e-5
+    S_f = lw.lw_spectrum(torch.from_numpy(rec.astype(np.float32)).cuda(), lw.LW_MIXED_F32,
+                         n_pix, grid)
+    assert rel_l2(S_f.double().cpu().numpy(), S_o) <= 1e-5
 
 
 def test_status_word_reports_bad_inputs():
@@ -146,7 +149,7 @@ def test_status_word_reports_bad_inputs():
     t[7] = t[6]
     bad = simple.Trajectories(t, tr.r, b, tr.beta_dot)
     grid = lw.Grid(tr.t[0], 1e-18, 64)
-    for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN):
+    for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32):
         g = gpu_run(bad, n_hat, grid, prec, spectrum=False)
         assert g["status"] & lw.LW_ST_BETA and g["status"] & lw.LW_ST_TIME
 

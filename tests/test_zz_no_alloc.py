@@ -20,7 +20,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("n_bins,n_pix", [(4096, 64), (8192, 5), (65536, 7)])
-@pytest.mark.parametrize("precision", [lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN])
+@pytest.mark.parametrize("precision", [lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN,
+                                       lw.LW_MIXED_F32])
 def test_static_scratch_matches_workspace_entry_point(n_bins, n_pix, precision):
     grid = lw.Grid(0.0, 2.9e-18, n_bins)
     tol = 1e-12 if precision == lw.LW_FP64 else 1e-5
@@ -31,6 +32,8 @@ def test_static_scratch_matches_workspace_entry_point(n_bins, n_pix, precision):
             hi = rec.astype(np.float32)
             lo = (rec - hi.astype(np.float64)).astype(np.float32)
             r = torch.from_numpy(np.stack([hi, lo], -1)).cuda()
+        elif precision == lw.LW_MIXED_F32:
+            r = torch.from_numpy(rec.astype(np.float32)).cuda()
         else:
             r = torch.from_numpy(rec).cuda()
         S_ref, X_ref = lw.lw_spectrum(r, precision, n_pix, grid, want_X=True)
