@@ -125,3 +125,20 @@ int main(void) {
                                                 lw.lw_grid, lw.lw_batch_item, lw.lw_batch)]
     assert offs == [lw.lw_traj.t.offset, lw.lw_traj.input_status.offset,
                     lw.lw_batch_item.grid.offset, lw.lw_batch_item.e_chunk.offset]
+
+
+def test_enum_values_match_the_header(tmp_path):
+    """The binding's precision, field, status and section constants are the header's."""
+    import subprocess
+    names = ["LW_FP64", "LW_MIXED", "LW_MIXED_KAHAN", "LW_MIXED_F32", "LW_FIELD_ACCEL",
+             "LW_FIELD_VELOCITY", "LW_ST_BETA", "LW_ST_NONFINITE", "LW_ST_TIME", "LW_ST_CLIP",
+             "LW_ST_TA_ORDER", "LW_ST_STEP", "LW_SECTION_FP64", "LW_SECTION_MIXED"]
+    src = tmp_path / "enums.c"
+    src.write_text("#include <stdio.h>\n#include \"lw.h\"\nint main(void) {\n" +
+                   "".join(f'  printf("%d\\n", (int){n});\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert [int(x) for x in out] == [getattr(lw, n) for n in names]
