@@ -21,11 +21,12 @@
 // and evaluated per sample with three FP32 FMAs of small, block-relative
 // quantities.  Because t_a increases along a subluminal trajectory, a block
 // needs one coordinate per pixel (its last sample) to know which grid points
-// it reaches; each grid point's step is then found by bisection over the
-// staged block.  The field is FP32 in the stable form
+// it reaches; each grid point's step is then found by a bracketed search
+// (regula falsi, then bisection) over the staged block.  The field is FP32 in
+// the stable form
 //   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
-// and contributions are added with FP64 atomics (or a compensated pair of
-// FP32 atomics).
+// and contributions are added with FP64 atomics, a compensated pair of FP32
+// atomics, or FP32 atomics (the three mixed records).
 #include <math.h>
 
 #include <algorithm>
@@ -352,8 +353,8 @@ __host__ __device__ constexpr size_t stage_bytes(int B) {
 // block of samples reaches form one run (j_done, j_end], where j_end follows
 // from the block's last sample alone, and each of them lies in exactly one
 // step (t_{i-1}, t_i] of Algorithm 2: the first sample i whose coordinate
-// reaches it, found by bisection over the staged block.  Per block a lane
-// evaluates one coordinate per pixel; the grid points of the warp's 128
+// reaches it, found by a bracketed search over the staged block.  Per block a lane
+// evaluates one coordinate per pixel; the grid points of the warp's 32 * PIX
 // pixels are then spread over its 32 lanes (prefix sum of the runs, one grid
 // point per lane and round), each lane finding its step, evaluating the two
 // fields and adding the interpolated value.  Blocks are staged into two
