@@ -652,7 +652,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mixed", default="f32", choices=["f32", "f64"],
                     help="record of the timed mixed path: FP32 (LW_MIXED_F32) or FP64 (LW_MIXED)")
-    ap.add_argument("--e2e-chunks", type=int, default=8)
+    ap.add_argument("--e2e-chunks", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
