@@ -285,7 +285,8 @@ constexpr int kMaxWarpJobs = 1 << 20;
 // located by bisection over the slots' job offsets.
 constexpr int kJobTable = 128;
 // Step searches: regula falsi (linear interpolation inside the bracket) for this many
-// probes, then bisection.  On the C2 trajectories it needs 2.1 probes per grid point
+// probes, then bisection.  On Boris trajectories of a 10,000-electron bunch in a
+// 0.8 um laser (10,000 steps, 64 x 64 pixels, 65,536 bins) it needs 2.1 probes per grid point
 // on average (at most 5); alternating interpolation and bisection needed 3.2.
 constexpr int kFalsiProbes = 8;
 
