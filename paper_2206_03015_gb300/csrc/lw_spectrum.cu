@@ -7,15 +7,18 @@
 // z = a + i b; with Z = FFT(z):
 //   A(l) = (Z_l + conj Z_{N-l}) / 2,   B(l) = (Z_l - conj Z_{N-l}) / (2i).
 // A pixel pair (m0, m1) gives three sequences: (x0 + i y0), (x1 + i y1),
-// (z0 + i z1).  Transforms are radix-2 in shared memory with twiddles read
-// from a table e^{+2 pi i t/N} built once per call:
+// (z0 + i z1).  Transforms run in shared memory as passes of up to four radix-2
+// stages (lw_fft.cuh: each group pre-multiplied by twiddles from a table
+// e^{+2 pi i t/N} built once per call, then constant-root stages):
 //   N <= 4096   one CTA per pixel pair, all three sequences in turn;
 //   N >  4096   four-step: N = N1 * N2, pass 1 transforms the N2 columns of
 //               length N1 (coalesced column tiles) and applies the twiddles
-//               e^{2 pi i j2 l1 / N}, pass 2 transforms each row l1 together
-//               with its mirror row N1 - l1, which holds the Z_{N-l} needed by
+//               e^{2 pi i j2 l1 / N}, pass 2 transforms rows l1 .. l1+3 together
+//               with their mirror rows N1 - l1, which hold the Z_{N-l} needed by
 //               the split above, for the three sequences of a pixel pair at
-//               once, so each spectrum value is written exactly once.
+//               once, so each spectrum value is written exactly once.  Both
+//               passes are instantiated per row length (2^6 .. 2^9) with the
+//               pass plan fixed at compile time.
 #include <math.h>
 
 #include <algorithm>
