@@ -27,8 +27,12 @@
  *  - Data-dependent conditions found by the kernels are OR-ed into the
  *    caller's device status word (int32, LW_ST_* bits); read it after the
  *    stream has been synchronised.  Kernels never trap.
- *  - The library holds no global state; calls on different streams may run
- *    concurrently as long as they do not write the same buffers.
+ *  - Calls on different streams may run concurrently as long as they do not
+ *    write the same buffers.  Two entry points hold global state and must be
+ *    serialised (one stream, or host-side ordering): lw_batch_deposit copies
+ *    the batch's arguments into a constant-memory table of the library, and
+ *    lw_spectrum_static uses one file-scope device scratch array.  Every other
+ *    call keeps its state in caller buffers.
  *
  * Units are SI: t [s], r [m], beta [1], beta_dot [1/s].  Field records hold
  * the LW far field divided by the constant q/(4 pi eps0 c0 R), i.e.

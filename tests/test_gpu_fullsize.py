@@ -21,6 +21,11 @@ FP64_TOL = 1e-9
 MIXED_TOL = 1e-4
 # corners, the axis and two off-axis pixels of the 64 x 64 detector
 SAMPLE = [0, 63, 2080, 1000, 3333, 4095]
+# every precision: FP64, and the mixed path with its three records (FP64, compensated FP32
+# pairs, plain FP32 -- the last is the one the benchmark times)
+MODES = {"fp64": lw.LW_FP64, "mixed": lw.LW_MIXED, "mixed_kahan": lw.LW_MIXED_KAHAN,
+         "mixed_f32": lw.LW_MIXED_F32}
+MIXED = ["mixed", "mixed_kahan", "mixed_f32"]
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +42,7 @@ def c2():
     b = lw.lw_grid_bounds(traj, det).cpu().numpy()
     grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
     out = {"w": w, "grid": grid}
-    for name, prec in (("mixed", lw.LW_MIXED), ("fp64", lw.LW_FP64)):
+    for name, prec in MODES.items():
         status = torch.zeros(1, dtype=torch.int32, device=dev)
         rec = lw.lw_deposit_time_domain(traj, det, grid, prec, status=status)
         S = lw.lw_spectrum(rec, prec, det.n_pix, grid)
@@ -61,15 +66,20 @@ def test_c2_fp64_sampled_pixels_match_oracle(c2):
         assert rel_l2(g["S"][m].cpu().numpy(), o["S"][k]) <= FP64_TOL, m
 
 
-def test_c2_mixed_sampled_pixels_match_oracle(c2):
-    g, o = c2["mixed"], c2["oracle"]
+@pytest.mark.parametrize("mode", MIXED)
+def test_c2_mixed_sampled_pixels_match_oracle(c2, mode):
+    g, o = c2[mode], c2["oracle"]
     assert o["status"] & ~g["status"] == 0
     for k, m in enumerate(SAMPLE):
         assert rel_l2(g["S"][m].cpu().numpy(), o["S"][k]) <= MIXED_TOL, m
+        # the record itself, element-wise against the oracle's largest value
+        scale = np.abs(o["rec"][k]).max()
+        assert np.abs(g["rec"][k] - o["rec"][k]).max() <= MIXED_TOL * scale, m
 
 
-def test_c2_mixed_matches_fp64_over_all_pixels(c2):
-    a, b = c2["mixed"]["S"], c2["fp64"]["S"]
+@pytest.mark.parametrize("mode", MIXED)
+def test_c2_mixed_matches_fp64_over_all_pixels(c2, mode):
+    a, b = c2[mode]["S"], c2["fp64"]["S"]
     err = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
     assert err <= MIXED_TOL, err
     # per pixel as well: no pixel's spectrum is off by more than the tolerance
