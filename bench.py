@@ -9,9 +9,12 @@ timed beside it and the mixed spectrum is compared with the FP64 one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  For N > 1 (torchrun) each rank owns its own
-detector (weak scaling, the paper's detector parallelization): no collective
-touches the data path; a barrier and a MAX over ranks bracket the timing.
+Prints one JSON line (rank 0).  For N > 1 (torchrun) the detector's pixels are
+split into one contiguous block per rank (the paper's detector parallelization,
+strong scaling: the whole job is one detector); every rank holds all
+trajectories and the same observer grid, and no collective touches the data
+path -- a barrier and a MAX over ranks bracket the timing.  ``--shard detectors``
+gives every rank a detector of its own instead (weak scaling).
 """
 from __future__ import annotations
 
@@ -149,10 +152,25 @@ def grid_points_reached(t, r, det, grid, chunk=256):
 
 # ----------------------------------------------------------------------------- workload
 
+def shard_pixels(n_pix, rank, world, shard="pixels"):
+    """[lo, hi) of the detector's pixels this rank deposits: one contiguous block of the
+    detector per rank (Sec. 4.2, detector parallelization), or all of them when every
+    rank observes a detector of its own (``shard == "detectors"``)."""
+    from paper_2206_03015_gb300 import parallel
+    if world == 1 or shard == "detectors":
+        return 0, n_pix
+    return parallel.pixel_shard(n_pix, rank, world)
+
+
+def job_deposits(n_e, n_s, n_pix, world, shard="pixels"):
+    """Deposits of the whole job (all ranks): one detector, or one per rank."""
+    return n_e * n_s * n_pix * (world if shard == "detectors" else 1)
+
+
 def make_workload(args, rank):
     from workloads import configs
     w = configs.c2_paper(n_e=args.n_e, n_s=args.n_s, nx=args.nx, n_bins=args.n_bins)
-    if rank > 0:
+    if rank > 0 and args.shard == "detectors":
         # weak scaling: rank r observes its own detector, rotated about the beam axis
         ang = rank * 2.0 * math.pi / max(args.world, 1) * 0.5
         c, s = math.cos(ang), math.sin(ang)
@@ -174,21 +192,27 @@ def run_ours(args, rank, world, dist):
     w = make_workload(args, rank)
     t_gen = time.time() - t_gen
     tr = w.traj
-    n_dep = w.deposits
     # device-resident FP64 inputs
     t_d = torch.from_numpy(tr.t).to(dev)
     r_d = torch.from_numpy(tr.r).to(dev)
     b_d = torch.from_numpy(tr.beta).to(dev)
     a_d = torch.from_numpy(tr.beta_dot).to(dev)
-    det = lw.Detector(w.n_hat, device=dev)
-    # grid (Eqs. tu_min, tu_max) once; it is fixed for the workload
+    # grid (Eqs. tu_min, tu_max) once, from the whole detector, so that every rank's
+    # pixel block shares it; it is fixed for the workload
     traj0 = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_MIXED,
                                       block=args.block, device=dev)
-    bnd = lw.lw_grid_bounds(traj0, det).cpu().numpy()
+    bnd = lw.lw_grid_bounds(traj0, lw.Detector(w.n_hat, device=dev)).cpu().numpy()
     grid = lw.grid_from_bounds(bnd[0], bnd[1], w.n_bins)
+    p_lo, p_hi = shard_pixels(w.n_pix, rank, world, args.shard)
+    w.n_hat = np.ascontiguousarray(w.n_hat[p_lo:p_hi])
+    w.theta_x, w.theta_y = w.theta_x[p_lo:p_hi], w.theta_y[p_lo:p_hi]
+    det = lw.Detector(w.n_hat, device=dev)
+    n_dep = w.deposits                                     # this rank's deposits
+    n_job = job_deposits(tr.n_e, tr.n_s, w.n_pix if args.shard == "detectors" else
+                         args.nx * args.nx, world, args.shard)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     # the timed mixed path: FP32 record (LW_MIXED_F32) by default, FP64 record with --mixed f64
-    MIX = lw.LW_MIXED_F32 if args.mixed == "f32" else lw.LW_MIXED
+    MIX = {"f32": lw.LW_MIXED_F32, "x4": lw.LW_MIXED_F32X4, "f64": lw.LW_MIXED}[args.mixed]
     shp, dt = lw.record_shape(det, grid, MIX)
     rec_m = torch.empty(shp, dtype=dt, device=dev)
     S_m = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float32, device=dev)
@@ -246,20 +270,27 @@ def run_ours(args, rank, world, dist):
     ms_m, clocks = timed_loop(step_mixed, args.steps, args.warmup, sampler)
     ms_step = ms_m / args.steps
     dep_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_dep)
-    value = n_dep * world / (ms_step * 1e-3)
+    value = n_job / (ms_step * 1e-3)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak" if args.shard == "detectors" else "strong", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.full else f"c2_paper reduced: {args.n_e} e x "
                    f"{args.n_s} steps x {args.nx}x{args.nx} px, {args.n_bins} bins",
                    "n_e": tr.n_e, "n_s": tr.n_s, "n_pix": w.n_pix, "n_bins": w.n_bins,
                    "deposits_per_step_per_gpu": n_dep, "block": args.block,
-                   "precision": ("LW_MIXED_F32 (FP32 record)" if MIX == lw.LW_MIXED_F32
-                                 else "LW_MIXED (FP64 record)"),
+                   "precision": {lw.LW_MIXED_F32: "LW_MIXED_F32 (FP32 record)",
+                                 lw.LW_MIXED_F32X4: "LW_MIXED_F32X4 (FP32 record, x/y/z "
+                                                    "interleaved per grid point)",
+                                 lw.LW_MIXED: "LW_MIXED (FP64 record)"}[MIX],
                    "l2": "inputs larger than L2 (mixed trajectory section %.1f GB)"
                          % (traj0.ws.numel() / 1e9),
-                   "parallelism": f"detector-sharded x{world} (one detector per GPU)",
+                   "parallelism": (f"detector parallelization: one detector per GPU x{world}"
+                                   if args.shard == "detectors" else
+                                   f"detector parallelization: pixels {p_lo}..{p_hi - 1} of "
+                                   f"one detector on each of {world} GPU(s)"),
+                   "deposits_per_step_job": n_job,
                    "generation_s": round(t_gen, 1)},
     }
     # roofline of the dominant kernel (mixed deposit) against HBM: the algorithmic bytes
@@ -291,7 +322,7 @@ def run_ours(args, rank, world, dist):
                           "atomics_per_s": 3.0 * n_points / (dep_ms * 1e-3)}
     result["clocks"] = clocks
     # the other mixed record beside it (FP64 record when the FP32 one is timed)
-    if MIX == lw.LW_MIXED_F32:
+    if MIX != lw.LW_MIXED:
         rec_64 = torch.empty(lw.record_shape(det, grid, lw.LW_MIXED)[0], dtype=torch.float64,
                              device=dev)
         S_64m = torch.empty_like(S_m)
@@ -305,7 +336,7 @@ def run_ours(args, rank, world, dist):
 
         ms_64m, _ = timed_loop(step_mixed64, args.steps, args.warmup)
         result["mixed_fp64_record"] = {"ms_per_step": ms_64m / args.steps,
-                                       "value": n_dep * world / (ms_64m / args.steps * 1e-3)}
+                                       "value": n_job / (ms_64m / args.steps * 1e-3)}
         del rec_64, S_64m
     torch.cuda.synchronize()
     st_m = int(status.item())
@@ -401,7 +432,7 @@ def run_ours(args, rank, world, dist):
         ms_e, _ = timed_loop(step_e2e, args.steps, min(args.warmup, 3), None,
                              (s_cp, s_pr, s_dp, s_bk))
         h2d = sum(x.numel() * x.element_size() for x in h)
-        result["e2e"] = {"value": n_dep * world / (ms_e / args.steps * 1e-3), "unit": UNIT,
+        result["e2e"] = {"value": n_job / (ms_e / args.steps * 1e-3), "unit": UNIT,
                          "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": S_host[0].numel() * S_host[0].element_size(),
                          "ms_per_step": ms_e / args.steps,
@@ -431,7 +462,7 @@ def run_ours(args, rank, world, dist):
 
         k64 = max(1, min(args.steps, args.fp64_steps))
         ms_d, _ = timed_loop(step_fp64, k64, 1)
-        fp64 = {"value": n_dep * world / (ms_d / k64 * 1e-3), "ms_per_step": ms_d / k64,
+        fp64 = {"value": n_job / (ms_d / k64 * 1e-3), "ms_per_step": ms_d / k64,
                 "steps": k64, "warmup": 1}
         S_64 = S_d
     # accuracy of the mixed spectrum against the FP64 GPU spectrum (parity-tested vs oracle)
@@ -650,12 +681,16 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mixed", default="f32", choices=["f32", "f64"],
-                    help="record of the timed mixed path: FP32 (LW_MIXED_F32) or FP64 (LW_MIXED)")
+    ap.add_argument("--mixed", default="f32", choices=["f32", "x4", "f64"],
+                    help="record of the timed mixed path: FP32 (LW_MIXED_F32), FP32 interleaved "
+                         "(LW_MIXED_F32X4) or FP64 (LW_MIXED)")
     ap.add_argument("--e2e-chunks", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--shard", default="pixels", choices=["pixels", "detectors"],
+                    help="N > 1: split one detector's pixels (strong scaling) or give each "
+                         "rank a detector of its own (weak scaling)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5"])
     ap.add_argument("--c5-variants", type=int, default=64)
     ap.add_argument("--c5-ne", type=int, nargs=2, default=(128, 1024))

@@ -67,12 +67,16 @@ enum {
                       the L2 (red.global.add.f64), FP32 FFT */
     LW_MIXED_KAHAN = 2, /* as LW_MIXED but the record is a compensated FP32 pair
                            (sum, compensation): atomic add with return + two-sum */
-    LW_MIXED_F32 = 3    /* as LW_MIXED but the record is FP32, added to by the L2
+    LW_MIXED_F32 = 3,   /* as LW_MIXED but the record is FP32, added to by the L2
                            (red.global.add.f32): half the record's bytes and faster
                            atomics; each bin's sum carries FP32 rounding, so it suits
                            records whose bins collect few contributions each (about 3 for
                            a 10,000-electron bunch on 64 x 64 pixels and 65,536 bins; the
                            error grows with the count) */
+    LW_MIXED_F32X4 = 4  /* as LW_MIXED_F32 with the three components of a grid point
+                           stored together as (x, y, z, 0) and added by one vector
+                           reduction (red.global.add.v4.f32): one L2 operation per grid
+                           point instead of three, for a third more record bytes */
 };
 
 /* Field terms (bit mask) of lw_deposit_time_domain. */
@@ -198,13 +202,14 @@ int lw_grid_bounds(const lw_traj* traj, const lw_detector* det, double* bounds, 
  *   D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp,
  *   F = [(n - beta)(n . beta_dot) - D beta_dot] / D^3,
  * and accumulates into FP64 (LW_MIXED), compensated FP32 pairs (LW_MIXED_KAHAN)
- * or FP32 (LW_MIXED_F32).
- *   precision    LW_FP64, LW_MIXED, LW_MIXED_KAHAN or LW_MIXED_F32 (the matching
- *                section must exist)
+ * or FP32 (LW_MIXED_F32, and LW_MIXED_F32X4 with the components interleaved).
+ *   precision    LW_FP64, LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32 or LW_MIXED_F32X4
+ *                (the matching section must exist)
  *   field_flags  LW_FIELD_* mask (non-zero)
  *   record       device; LW_FP64 and LW_MIXED: double [n_pix][3][n_bins];
  *                LW_MIXED_KAHAN: float2 [n_pix][3][n_bins] = (sum, compensation),
- *                value = sum + compensation; LW_MIXED_F32: float [n_pix][3][n_bins]
+ *                value = sum + compensation; LW_MIXED_F32: float [n_pix][3][n_bins];
+ *                LW_MIXED_F32X4: float4 [n_pix][n_bins] = (x, y, z, 0)
  *   accumulate   0: the record is zeroed first; 1: add to its contents
  *   status       device int32, OR-ed with LW_ST_* bits (may be NULL)
  * Grid points outside [0, n_bins) are skipped (LW_ST_CLIP).
@@ -303,7 +308,8 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
 
 /* Several independent problems ("variants": own trajectories, detector, grid
  * and record) deposited by one persistent launch of the mixed-precision
- * deposit (LW_MIXED, LW_MIXED_KAHAN or LW_MIXED_F32).  The work is cut into units of
+ * deposit (LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32 or LW_MIXED_F32X4).  The work is
+ * cut into units of
  * (variant, 512-pixel tile, chunk of electrons) that resident CTAs take from a
  * list: variants largest first, each variant's chunks in arrival order (the
  * upload's electron order) with its tiles fastest, so variants of very
@@ -328,7 +334,7 @@ typedef struct {
     const lw_traj* traj;        /* uploaded with the mixed section */
     const lw_detector* det;
     lw_grid grid;
-    void* record;               /* 8 bytes per value, layout of lw_deposit_time_domain */
+    void* record;               /* layout of lw_deposit_time_domain for the precision */
     int32_t* status;            /* device int32 or NULL */
     int32_t e_chunk;            /* electrons per work unit, 0 = automatic */
 } lw_batch_item;

@@ -13,6 +13,7 @@ from .lw import (  # noqa: F401
     LW_MIXED,
     LW_MIXED_KAHAN,
     LW_MIXED_F32,
+    LW_MIXED_F32X4,
     LW_SECTION_FP64,
     LW_SECTION_MIXED,
     grid_from_bounds,

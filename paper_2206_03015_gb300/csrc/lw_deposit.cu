@@ -261,7 +261,7 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* _
     F[0] = F[1] = F[2] = 0.0f;
     if (!(D > 0.0f)) return;
     const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
-    const float invD = __frcp_rn(D);
+    const float invD = __fdividef(1.0f, D);   // rcp.approx: 1 ulp, far below the FP32 field's own error
     const float invD3 = invD * invD * invD;
     if (flags & LW_FIELD_ACCEL) {
         const float na = fmaf(pc.nz, az, fmaf(pc.ny, ay, pc.nx * ax));
@@ -291,8 +291,10 @@ constexpr int kJobTable = 128;
 constexpr int kFalsiProbes = 8;
 
 // Record accumulation of the mixed modes: FP64 (red.global.add.f64), compensated FP32
-// pair, or FP32 (red.global.add.f32).
-enum { kAccF64 = 0, kAccKahan = 1, kAccF32 = 2 };
+// pair, FP32 (red.global.add.f32), or FP32 interleaved per grid point as (x, y, z, 0) and
+// added by one vector reduction (red.global.add.v4.f32: one L2 sector operation instead of
+// three).
+enum { kAccF64 = 0, kAccKahan = 1, kAccF32 = 2, kAccF32X4 = 3 };
 
 template <int ACC>
 __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
@@ -305,8 +307,33 @@ __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
     }
 }
 
-__host__ __device__ constexpr size_t record_elem_bytes(int precision) {
-    return precision == LW_MIXED_F32 ? 4 : 8;   // float, or double / float2
+// Adds the three components (v0, v1, v2) of grid point j of pixel m.
+template <int ACC>
+__device__ __forceinline__ void deposit3(void* rec, int64_t m, int64_t j, int64_t n_bins,
+                                         float v0, float v1, float v2) {
+    if (ACC == kAccF32X4) {
+        float* p = static_cast<float*>(rec) + ((m * n_bins + j) << 2);
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v0),
+                     "f"(v1), "f"(v2), "f"(0.0f)
+                     : "memory");
+    } else {
+        const int64_t idx = m * 3 * n_bins + j;
+        accumulate<ACC>(rec, idx, v0);
+        accumulate<ACC>(rec, idx + n_bins, v1);
+        accumulate<ACC>(rec, idx + 2 * n_bins, v2);
+    }
+}
+
+// Accumulation form and record size of a precision.
+__host__ __device__ constexpr int acc_of(int precision) {
+    return precision == LW_MIXED_KAHAN ? kAccKahan
+           : precision == LW_MIXED_F32 ? kAccF32
+           : precision == LW_MIXED_F32X4 ? kAccF32X4 : kAccF64;
+}
+// 4-byte words per (pixel, grid point): three doubles or float pairs, three floats, or
+// one float4
+__host__ __device__ constexpr int record_words(int precision) {
+    return precision == LW_MIXED_F32 ? 3 : precision == LW_MIXED_F32X4 ? 4 : 6;
 }
 
 // FP64 bin index of a trajectory end sample, with the FP64 path's operation order.
@@ -544,12 +571,10 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 float Fb[3], Fa[3];
                 field_fp32(pc, s_field2 + 3 * i, p.flags, c0_over_R, Fb);
                 field_fp32(pc, s_field2 + 3 * (i + 1), p.flags, c0_over_R, Fa);
-                const float wb = du > 0.0f ? a0 * __frcp_rn(du) : 0.0f;
+                const float wb = du > 0.0f ? __fdividef(a0, du) : 0.0f;
                 const float wa = 1.0f - wb;
-                const int64_t idx = slot_pixel(sl) * 3 * p.n_bins + j;
-                accumulate<ACC>(p.record, idx, fmaf(Fb[0], wa, Fa[0] * wb));
-                accumulate<ACC>(p.record, idx + p.n_bins, fmaf(Fb[1], wa, Fa[1] * wb));
-                accumulate<ACC>(p.record, idx + 2 * p.n_bins, fmaf(Fb[2], wa, Fa[2] * wb));
+                deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, fmaf(Fb[0], wa, Fa[0] * wb),
+                              fmaf(Fb[1], wa, Fa[1] * wb), fmaf(Fb[2], wa, Fa[2] * wb));
             };
             // a job handed to the warp: the slot's block data from shared memory
             auto job = [&](int sl, int j) {
@@ -940,12 +965,12 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     }
 }
 
-// Zeroes every variant's record (n_pix * 3 * n_bins values of 8 bytes): grid y =
+// Zeroes every variant's record (n_pix * n_bins * words 4-byte words): grid y =
 // variant, x = CTAs striding over it, with 16-byte stores where the record is
 // 16-byte aligned (an odd last value is stored alone).
-__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int elem_bytes) {
+__global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int words) {
     const DepositArgs& a = vars[blockIdx.y];
-    const int64_t n = a.n_pix * 3 * a.n_bins * (elem_bytes / 4);   // 4-byte words
+    const int64_t n = a.n_pix * a.n_bins * words;   // 4-byte words
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     float* rec = static_cast<float*>(a.record);
@@ -973,15 +998,14 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     if ((field_flags & LW_FIELD_VELOCITY) && !(det->R > 0.0)) return LW_EINVAL;
     if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
-        precision != LW_MIXED_F32)
+        precision != LW_MIXED_F32 && precision != LW_MIXED_F32X4)
         return LW_EINVAL;
     if (precision == LW_FP64 && !(traj->sections & LW_SECTION_FP64)) return LW_EINVAL;
     if (precision != LW_FP64 && !(traj->sections & LW_SECTION_MIXED)) return LW_EINVAL;
     cudaStream_t st = as_stream(stream);
-    const size_t elem = record_elem_bytes(precision);
     if (!accumulate &&
-        cudaMemsetAsync(record, 0, elem * 3 * (size_t)(det->n_pix * grid->n_bins), st) !=
-            cudaSuccess)
+        cudaMemsetAsync(record, 0, 4 * (size_t)record_words(precision) *
+                                       (size_t)(det->n_pix * grid->n_bins), st) != cudaSuccess)
         return LW_ECUDA;
 
     DepositArgs a{};
@@ -1027,9 +1051,11 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
     const size_t smem = 2 * stage_bytes(traj->block);   // double-buffered staging
     // static tables + double-buffered staging exceed the 48 KB default: opt in
-    auto kern = precision == LW_MIXED_KAHAN ? deposit_mixed_kernel<PIX, kAccKahan>
-                : precision == LW_MIXED_F32 ? deposit_mixed_kernel<PIX, kAccF32>
-                                            : deposit_mixed_kernel<PIX, kAccF64>;
+    const int acc = acc_of(precision);
+    auto kern = acc == kAccKahan ? deposit_mixed_kernel<PIX, kAccKahan>
+                : acc == kAccF32 ? deposit_mixed_kernel<PIX, kAccF32>
+                : acc == kAccF32X4 ? deposit_mixed_kernel<PIX, kAccF32X4>
+                                   : deposit_mixed_kernel<PIX, kAccF64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return LW_ECUDA;
@@ -1067,7 +1093,8 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
     constexpr int PIX = kMixPix;
     if (!items || n_items < 1 || !ws_bytes || !plan) return LW_EINVAL;
     if (n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
-    if (precision != LW_MIXED && precision != LW_MIXED_KAHAN && precision != LW_MIXED_F32)
+    if (precision != LW_MIXED && precision != LW_MIXED_KAHAN && precision != LW_MIXED_F32 &&
+        precision != LW_MIXED_F32X4)
         return LW_EUNSUPPORTED;
     if (field_flags == 0 || (field_flags & ~(LW_FIELD_ACCEL | LW_FIELD_VELOCITY))) return LW_EINVAL;
     std::vector<DepositArgs> vars((size_t)n_items);
@@ -1190,15 +1217,17 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     const BatchUnit* units = reinterpret_cast<const BatchUnit*>(base + plan->offsets[2]);
     if (plan->n_items > kBatchMaxItems) return LW_EUNSUPPORTED;
     zero_records_kernel<<<dim3(kSms * 4, (unsigned)plan->n_items), 256, 0, st>>>(
-        vars, (int)record_elem_bytes(plan->precision));
+        vars, record_words(plan->precision));
     if (launch_status() != LW_OK) return LW_ECUDA;
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return LW_ECUDA;
     if (cudaMemcpyToSymbolAsync(c_batch_vars, vars, sizeof(DepositArgs) * (size_t)plan->n_items,
                                 0, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return LW_ECUDA;
-    auto kern = plan->precision == LW_MIXED_KAHAN ? deposit_batched_kernel<PIX, kAccKahan>
-                : plan->precision == LW_MIXED_F32 ? deposit_batched_kernel<PIX, kAccF32>
-                                                  : deposit_batched_kernel<PIX, kAccF64>;
+    const int acc = acc_of(plan->precision);
+    auto kern = acc == kAccKahan ? deposit_batched_kernel<PIX, kAccKahan>
+                : acc == kAccF32 ? deposit_batched_kernel<PIX, kAccF32>
+                : acc == kAccF32X4 ? deposit_batched_kernel<PIX, kAccF32X4>
+                                   : deposit_batched_kernel<PIX, kAccF64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              plan->smem_bytes) != cudaSuccess)
         return LW_ECUDA;

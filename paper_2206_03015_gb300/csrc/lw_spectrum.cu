@@ -30,7 +30,7 @@ namespace lw {
 namespace {
 
 // Record formats of the mixed modes.
-enum { kRecF64 = 0, kRecKahan = 1, kRecF32 = 2 };
+enum { kRecF64 = 0, kRecKahan = 1, kRecF32 = 2, kRecF32X4 = 3 };
 
 // Record readers.  load() fetches an element's raw bits, cvt() turns them into T; pass 1
 // issues a batch of loads before it converts any, so that they are all in flight.
@@ -48,15 +48,22 @@ template <> struct RecReader<double> {
 template <> struct RecReader<float> {
     using Raw = uint2;   // a double, a (sum, compensation) float pair, or a float in .x
     const void* rec;
-    int kind;   // kRecF64 double, kRecKahan (sum, compensation) pairs, kRecF32 float
+    int kind;   // kRecF64 double, kRecKahan (sum, compensation) pairs, kRecF32 float,
+                // kRecF32X4 float4 (x, y, z, 0) per pixel and grid point
     __device__ uint2 load(int64_t row, int64_t N, int64_t j) const {
         if (kind == kRecF32)
             return make_uint2(__float_as_uint(__ldcs(static_cast<const float*>(rec) + row * N + j)),
                               0u);
+        if (kind == kRecF32X4) {   // row = 3 m + c
+            const int64_t m = row / 3;
+            return make_uint2(__float_as_uint(__ldcs(static_cast<const float*>(rec) +
+                                                     ((m * N + j) << 2) + (row - 3 * m))),
+                              0u);
+        }
         return __ldcs(static_cast<const uint2*>(rec) + row * N + j);
     }
     __device__ float cvt(uint2 v) const {   // double -> float on the integer pipe
-        if (kind == kRecF32) return __uint_as_float(v.x);
+        if (kind == kRecF32 || kind == kRecF32X4) return __uint_as_float(v.x);
         if (kind == kRecKahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
         return to_float_bits(v.y, v.x);   // little-endian double: v.y holds the high word
     }
@@ -64,7 +71,7 @@ template <> struct RecReader<float> {
     // pair this way and one on the integer pipe, which its index work already loads
     // (results differ only below the smallest normal float, which this one keeps)
     __device__ float cvt_fp64(uint2 v) const {
-        if (kind == kRecF32) return __uint_as_float(v.x);
+        if (kind == kRecF32 || kind == kRecF32X4) return __uint_as_float(v.x);
         if (kind == kRecKahan) return __uint_as_float(v.x) + __uint_as_float(v.y);
         return __double2float_rn(__hiloint2double((int)v.y, (int)v.x));
     }
@@ -455,7 +462,7 @@ extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
                            size_t* ws_bytes, void* stream) {
     if (!grid || !ws_bytes || n_pix < 1) return LW_EINVAL;
     if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
-        precision != LW_MIXED_F32)
+        precision != LW_MIXED_F32 && precision != LW_MIXED_F32X4)
         return LW_EINVAL;
     const int64_t N = grid->n_bins;
     if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;
@@ -466,7 +473,8 @@ extern "C" int lw_spectrum(const void* record, int32_t precision, int64_t n_pix,
         return run_spectrum<double>(record, 0, n_pix, grid, q, spectrum, X_save, ws, ws_bytes,
                                     st);
     const int kind = precision == LW_MIXED_KAHAN ? kRecKahan
-                     : precision == LW_MIXED_F32 ? kRecF32 : kRecF64;
+                     : precision == LW_MIXED_F32 ? kRecF32
+                     : precision == LW_MIXED_F32X4 ? kRecF32X4 : kRecF64;
     return run_spectrum<float>(record, kind, n_pix, grid, q, spectrum, X_save, ws, ws_bytes,
                                st);
 }
@@ -511,7 +519,7 @@ extern "C" int lw_spectrum_static(const void* record, int32_t precision, int64_t
                                   void* stream) {
     if (!grid || n_pix < 1 || !record || !spectrum) return LW_EINVAL;
     if (precision != LW_FP64 && precision != LW_MIXED && precision != LW_MIXED_KAHAN &&
-        precision != LW_MIXED_F32)
+        precision != LW_MIXED_F32 && precision != LW_MIXED_F32X4)
         return LW_EINVAL;
     const int64_t N = grid->n_bins;
     if (N < 2 || N > (int64_t(1) << 18) || (N & (N - 1))) return LW_EUNSUPPORTED;

@@ -19,7 +19,7 @@ import torch
 from . import build as _build
 
 LW_OK, LW_EINVAL, LW_ESIZE, LW_ECUDA, LW_EUNSUPPORTED, LW_ETIMEOUT = 0, -1, -2, -3, -4, -5
-LW_FP64, LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32 = 0, 1, 2, 3
+LW_FP64, LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32, LW_MIXED_F32X4 = 0, 1, 2, 3, 4
 LW_FIELD_ACCEL, LW_FIELD_VELOCITY = 1, 2
 LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER, LW_ST_STEP = 1, 2, 4, 8, 16, 32
 LW_SECTION_FP64, LW_SECTION_MIXED = 1, 2
@@ -293,11 +293,14 @@ def lw_grid_bounds(traj: Trajectories, det: Detector, out=None):
 
 def record_shape(det: Detector, grid: Grid, precision: int):
     """(shape, dtype) of the record: FP64 and MIXED accumulate in float64,
-    MIXED_KAHAN in (sum, compensation) float32 pairs, MIXED_F32 in float32."""
+    MIXED_KAHAN in (sum, compensation) float32 pairs, MIXED_F32 in float32,
+    MIXED_F32X4 in float32 (x, y, z, 0) per pixel and grid point."""
     if precision in (LW_FP64, LW_MIXED):
         return (det.n_pix, 3, grid.n_bins), torch.float64
     if precision == LW_MIXED_F32:
         return (det.n_pix, 3, grid.n_bins), torch.float32
+    if precision == LW_MIXED_F32X4:
+        return (det.n_pix, grid.n_bins, 4), torch.float32
     return (det.n_pix, 3, grid.n_bins, 2), torch.float32
 
 
@@ -305,6 +308,8 @@ def record_value(record: torch.Tensor, precision: int) -> torch.Tensor:
     """The record as float64 [n_pix][3][n_bins] (sum + compensation for MIXED_KAHAN)."""
     if precision == LW_MIXED_KAHAN:
         return record[..., 0].double() + record[..., 1].double()
+    if precision == LW_MIXED_F32X4:
+        return record[..., :3].permute(0, 2, 1).double()
     return record.double()
 
 

@@ -130,7 +130,7 @@ int main(void) {
 def test_enum_values_match_the_header(tmp_path):
     """The binding's precision, field, status and section constants are the header's."""
     import subprocess
-    names = ["LW_FP64", "LW_MIXED", "LW_MIXED_KAHAN", "LW_MIXED_F32", "LW_FIELD_ACCEL",
+    names = ["LW_FP64", "LW_MIXED", "LW_MIXED_KAHAN", "LW_MIXED_F32", "LW_MIXED_F32X4", "LW_FIELD_ACCEL",
              "LW_FIELD_VELOCITY", "LW_ST_BETA", "LW_ST_NONFINITE", "LW_ST_TIME", "LW_ST_CLIP",
              "LW_ST_TA_ORDER", "LW_ST_STEP", "LW_SECTION_FP64", "LW_SECTION_MIXED"]
     src = tmp_path / "enums.c"

@@ -39,7 +39,8 @@ def _records(variants, precision=lw.LW_MIXED):
     return recs
 
 
-@pytest.mark.parametrize("precision,tol", [(lw.LW_MIXED, 1e-12), (lw.LW_MIXED_F32, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(lw.LW_MIXED, 1e-12), (lw.LW_MIXED_F32, 1e-6),
+                                           (lw.LW_MIXED_F32X4, 1e-6)])
 def test_batched_equals_per_variant(variants, precision, tol):
     recs = _records(variants, precision)
     bp = lw.lw_batch_plan([v[2] for v in variants], [v[3] for v in variants],

@@ -21,11 +21,12 @@ FP64_TOL = 1e-9
 MIXED_TOL = 1e-4
 # corners, the axis and two off-axis pixels of the 64 x 64 detector
 SAMPLE = [0, 63, 2080, 1000, 3333, 4095]
-# every precision: FP64, and the mixed path with its three records (FP64, compensated FP32
-# pairs, plain FP32 -- the last is the one the benchmark times)
+# every precision: FP64, and the mixed path with each of its records (FP64, compensated FP32
+# pairs, plain FP32, FP32 interleaved per grid point -- the last is the one the benchmark
+# times)
 MODES = {"fp64": lw.LW_FP64, "mixed": lw.LW_MIXED, "mixed_kahan": lw.LW_MIXED_KAHAN,
-         "mixed_f32": lw.LW_MIXED_F32}
-MIXED = ["mixed", "mixed_kahan", "mixed_f32"]
+         "mixed_f32": lw.LW_MIXED_F32, "mixed_f32x4": lw.LW_MIXED_F32X4}
+MIXED = ["mixed", "mixed_kahan", "mixed_f32", "mixed_f32x4"]
 
 
 @pytest.fixture(scope="module")

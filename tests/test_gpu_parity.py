@@ -100,7 +100,8 @@ def test_fp64_record_and_spectrum(name):
 
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("block", [16, 128, 1024])
-@pytest.mark.parametrize("precision", [lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32])
+@pytest.mark.parametrize("precision", [lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32,
+                                       lw.LW_MIXED_F32X4])
 def test_mixed_record_and_spectrum(name, block, precision):
     tr, n_hat, grid, flags, R = _case(name)
     g = gpu_run(tr, n_hat, grid, precision, flags, R, block=block)
@@ -138,6 +139,11 @@ def test_spectrum_matches_oracle(n_bins, n_pix):
     S_f = lw.lw_spectrum(torch.from_numpy(rec.astype(np.float32)).cuda(), lw.LW_MIXED_F32,
                          n_pix, grid)
     assert rel_l2(S_f.double().cpu().numpy(), S_o) <= 1e-5
+    rec4 = np.zeros((n_pix, n_bins, 4), dtype=np.float32)
+    rec4[..., :3] = rec.transpose(0, 2, 1)
+    rec4[..., 3] = 1e30   # the fourth lane is never read
+    S_4 = lw.lw_spectrum(torch.from_numpy(rec4).cuda(), lw.LW_MIXED_F32X4, n_pix, grid)
+    assert rel_l2(S_4.double().cpu().numpy(), S_o) <= 1e-5
 
 
 def test_status_word_reports_bad_inputs():
@@ -149,7 +155,8 @@ def test_status_word_reports_bad_inputs():
     t[7] = t[6]
     bad = simple.Trajectories(t, tr.r, b, tr.beta_dot)
     grid = lw.Grid(tr.t[0], 1e-18, 64)
-    for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32):
+    for prec in (lw.LW_FP64, lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32,
+                 lw.LW_MIXED_F32X4):
         g = gpu_run(bad, n_hat, grid, prec, spectrum=False)
         assert g["status"] & lw.LW_ST_BETA and g["status"] & lw.LW_ST_TIME
 

@@ -93,3 +93,50 @@ def test_shards_partition_and_scheme_choice():
         mb = parallel.memory_per_rank("beam", 8, N_p, N_obs, N_Tu)
         md = parallel.memory_per_rank("detector", 8, N_p, N_obs, N_Tu)
         assert (pref == "detector") == (md <= mb)
+
+
+def _bench_module():
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_shard", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _bench_worker(rank, world, port, out_path):
+    """What bench.py does per rank under torchrun, without a GPU: its pixel block of the
+    one detector, its deposits, and the MAX over ranks of its step time."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b = _bench_module()
+        n_e, n_s, n_pix = 10_000, 10_000, 4096
+        lo, hi = b.shard_pixels(n_pix, rank, world)
+        mine = torch.tensor([lo, hi, n_e * n_s * (hi - lo)], dtype=torch.int64)
+        got = [torch.zeros(3, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(got, mine)
+        ms = torch.tensor([10.0 + rank], dtype=torch.float64)
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            torch.save({"shards": torch.stack(got), "ms": float(ms.item()),
+                        "job": b.job_deposits(n_e, n_s, n_pix, world)}, out_path)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_pixel_shards_cover_one_detector(tmp_path):
+    """bench.py --gpus 2: the two ranks' pixel blocks partition the detector, their
+    deposits add up to the job's, and the step time is the slower rank's."""
+    out = str(tmp_path / "bench.pt")
+    mp.start_processes(_bench_worker, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    got = torch.load(out)
+    sh = got["shards"].numpy()
+    assert sh[0][0] == 0 and sh[0][1] == sh[1][0] and sh[1][1] == 4096
+    assert int(sh[:, 2].sum()) == got["job"] == 10_000 * 10_000 * 4096
+    assert got["ms"] == 11.0
+    b = _bench_module()
+    assert b.shard_pixels(4096, 1, 2, "detectors") == (0, 4096)
+    assert b.job_deposits(10, 10, 4, 2, "detectors") == 800
