@@ -92,9 +92,11 @@ enum {
     LW_ST_TIME = 4,        /* lab time not strictly increasing along a trajectory */
     LW_ST_CLIP = 8,        /* grid points outside [0, n_bins) were skipped */
     LW_ST_TA_ORDER = 16,   /* advanced time not increasing between two samples (LW_FP64) */
-    LW_ST_STEP = 32        /* two consecutive samples at least c0 (t_i - t_(i-1)) apart
+    LW_ST_STEP = 32,       /* two consecutive samples at least c0 (t_i - t_(i-1)) apart
                               (checked by uploads with the FP64 section): the advanced time
                               may decrease for some direction */
+    LW_ST_TIMEOUT = 64     /* a kernel's bounded wait for its staged input ran out (the
+                              record is incomplete) */
 };
 
 /* Which device sections lw_trajectories_upload builds (bit mask). */
@@ -134,7 +136,9 @@ typedef struct {
                                tau = t - z/c0, _b = first sample of the sample's block */
     const void* field;      /* MIXED: float [n_e][n_s+1][6] (beta_x, beta_y, 1 - beta_z,
                                beta_dot_x, beta_dot_y, beta_dot_z) */
-    const double* anchor;   /* MIXED: double4 [n_e][n_blocks] (tau_b, x_b, y_b, z_b) */
+    const double* anchor;   /* MIXED: 32-byte records [n_e][n_blocks]: tau_b (double), then
+                               x_b, y_b, z_b as float pairs (hi, lo), hi = fl32(x),
+                               lo = fl32(x - hi) */
     const double* ends;     /* always: double [n_e][2][4] = (t, x, y, z) of the first and
                                the last sample of each electron */
     const int32_t* input_status; /* device int32: LW_ST_* found while uploading */
@@ -342,6 +346,7 @@ typedef struct {
 typedef struct {
     void* ws;
     int32_t n_items, n_units, precision, smem_bytes;
+    int32_t field_flags, reserved;
     int64_t offsets[3];
 } lw_batch;
 

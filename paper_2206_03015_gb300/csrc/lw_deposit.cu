@@ -46,7 +46,7 @@ struct DepositArgs {
     const double* bdot;
     const float4* scan;
     const float* field;
-    const D4* anchor;
+    const Anchor* anchor;
     int block, n_blocks;
     const int32_t* input_status;
     const double* ends;
@@ -222,7 +222,20 @@ __device__ void fp64_scan_cta(const DepositArgs& p) {
 
 constexpr int kMixThreads = 256;
 constexpr int kMixPix = 2;            // pixels per thread: tiles of 512 pixels
-constexpr int kMixMinBlocks = 3;      // resident CTAs per SM the register budget allows
+#ifndef LW_MIX_MIN_BLOCKS
+#define LW_MIX_MIN_BLOCKS 3
+#endif
+constexpr int kMixMinBlocks = LW_MIX_MIN_BLOCKS;   // resident CTAs per SM
+#ifndef LW_MIX_MAX_CHUNK
+#define LW_MIX_MAX_CHUNK 1
+#endif
+constexpr int kMixMaxChunk = LW_MIX_MAX_CHUNK;   // electrons per CTA at most
+// With the interleaved record one L2 sector takes a grid point's update, so a wider band of
+// electrons in flight costs little and several electrons per CTA share its pixel set-up.
+#ifndef LW_MIX_MAX_CHUNK_X4
+#define LW_MIX_MAX_CHUNK_X4 4
+#endif
+constexpr int kMixMaxChunkX4 = LW_MIX_MAX_CHUNK_X4;
 
 struct DF {   // unevaluated sum hi + lo of two floats
     float hi, lo;
@@ -250,32 +263,37 @@ struct PixelConst {
     float nx, ny, nz, omnz;   // direction and 1 - n_z (stable)
 };
 
-// Per-sample FP32 field in the stable form (zero if D <= 0).
+// Per-sample FP32 field in the stable form, for the field terms FL (LW_FIELD_* mask, a
+// compile-time constant); zero if D <= 0.
 // f: the sample's six field floats as three 8-byte-aligned pairs.
+template <int FL>
 __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* __restrict__ f,
-                                           uint32_t flags, float c0_over_R, float F[3]) {
+                                           float c0_over_R, float F[3]) {
     const float2 f01 = f[0], f23 = f[1], f45 = f[2];
     const float bx = f01.x, by = f01.y, eps = f23.x;
     const float ax = f23.y, ay = f45.x, az = f45.y;
     const float D = fmaf(-pc.ny, by, fmaf(-pc.nx, bx, fmaf(pc.nz, eps, pc.omnz)));
-    F[0] = F[1] = F[2] = 0.0f;
-    if (!(D > 0.0f)) return;
     const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
     const float invD = __fdividef(1.0f, D);   // rcp.approx: 1 ulp, far below the FP32 field's own error
     const float invD3 = invD * invD * invD;
-    if (flags & LW_FIELD_ACCEL) {
+    float F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    if (FL & LW_FIELD_ACCEL) {
         const float na = fmaf(pc.nz, az, fmaf(pc.ny, ay, pc.nx * ax));
-        F[0] = fmaf(mx, na, -D * ax) * invD3;
-        F[1] = fmaf(my, na, -D * ay) * invD3;
-        F[2] = fmaf(mz, na, -D * az) * invD3;
+        F0 = fmaf(mx, na, -D * ax) * invD3;
+        F1 = fmaf(my, na, -D * ay) * invD3;
+        F2 = fmaf(mz, na, -D * az) * invD3;
     }
-    if (flags & LW_FIELD_VELOCITY) {
+    if (FL & LW_FIELD_VELOCITY) {
         const float g2 = fmaf(-by, by, fmaf(-bx, bx, eps * (2.0f - eps)));   // 1 - beta^2
         const float g = c0_over_R * g2 * invD3;
-        F[0] = fmaf(mx, g, F[0]);
-        F[1] = fmaf(my, g, F[1]);
-        F[2] = fmaf(mz, g, F[2]);
+        F0 = fmaf(mx, g, F0);
+        F1 = fmaf(my, g, F1);
+        F2 = fmaf(mz, g, F2);
     }
+    const bool ok = D > 0.0f;   // selects: no branch around the loads
+    F[0] = ok ? F0 : 0.0f;
+    F[1] = ok ? F1 : 0.0f;
+    F[2] = ok ? F2 : 0.0f;
 }
 
 // Grid points of one pixel and block above which the owning lane deposits them
@@ -345,6 +363,14 @@ __device__ __forceinline__ int exact_bin(const double* e, double nx, double ny, 
     return (int)floor(u);
 }
 
+// The same, kept out of line: the mixed deposit needs it only for trajectory end samples
+// whose mixed bin coordinate lies within rounding of an integer, and a call keeps its
+// FP64 instructions out of the common path.
+__device__ __noinline__ int exact_bin_rare(const double* e, const double* n, double t_min,
+                                           double inv_dtu) {
+    return exact_bin(e, n[0], n[1], n[2], t_min, inv_dtu);
+}
+
 // Bin coordinate of a staged sample relative to its block's anchor, without the
 // anchor fraction f: u - I - f = s dtau + w . dr, with sc = (dtau, dr) and
 // w = (w_x, w_y, w_z) the pixel's slope (FP32 hi parts), s = 1/dt_u.
@@ -352,44 +378,111 @@ __device__ __forceinline__ float coord(float4 w, float s, float4 sc) {
     return fmaf(w.z, sc.w, fmaf(w.y, sc.z, fmaf(w.x, sc.y, s * sc.x)));
 }
 
-// Grid point J (relative to the anchor integer) is reached by a sample of
-// coordinate x when fl(J - f) <= x.  Returns the largest such J, by the same
-// FP32 comparison the crossing search makes, so the two always agree.
-__device__ __forceinline__ int last_point(float x, float f) {
-    const float s = fminf(fmaxf(__fadd_rn(x, f), -1.0e9f), 1.0e9f);
-    int J = (int)floorf(s);
-    if (__fsub_rn((float)(J + 1), f) <= x)
-        ++J;
-    else if (__fsub_rn((float)J, f) > x)
-        --J;
-    return J;
+// Staging of the mixed deposit: a ring of kMixStages shared buffers filled by the
+// tensor memory accelerator's bulk copies (cp.async.bulk, issued by one thread,
+// completion counted in bytes on one mbarrier per buffer), kMixStages - 1 blocks ahead
+// of the block being processed.  One buffer holds block b's samples i0 .. i0+B-1 as
+// float4 (block-relative light-front time and position), the field records of samples
+// i0 .. i0+B (the next block's first sample included) and, with block 0 and with every
+// block b of b % 32 == 31, the FP64 anchors of the next 32 blocks.
+#ifndef LW_MIX_STAGES
+#define LW_MIX_STAGES 2
+#endif
+constexpr int kMixStages = LW_MIX_STAGES;
+constexpr int kAnchorBatch = 32;
+__host__ __device__ constexpr size_t stage_field_off(int B) { return 16 * (size_t)B; }
+__host__ __device__ constexpr size_t stage_anchor_off(int B) {
+    // field records: 24 (B + 1) bytes copied from a 16-byte aligned start up to 8 bytes early
+    return (stage_field_off(B) + 24 * ((size_t)B + 1) + 8 + 15 + 31) / 32 * 32;
+}
+__host__ __device__ constexpr size_t stage_bytes(int B) {
+    return stage_anchor_off(B) + sizeof(Anchor) * kAnchorBatch;
 }
 
-// Asynchronous global -> shared copies (LDGSTS): the next block of samples is
-// staged while the current one is processed.
-// One staging buffer: B float4 samples and B+1 field records (the block's
-// samples preceded by the previous block's last one).
-__host__ __device__ constexpr size_t stage_bytes(int B) {
-    return (16 * (size_t)B + 24 * ((size_t)B + 1) + 31) / 32 * 32;
+// mbarrier and bulk-copy primitives (PTX ISA: mbarrier, cp.async.bulk).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of `bar` with the given parity to complete; gives up after a
+// bounded number of polls (each poll may suspend the thread for a hardware-chosen time)
+// and returns false.
+constexpr int kMaxPolls = 1 << 24;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int i = 0; i < kMaxPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Half-width of the band around an integer inside which a trajectory end sample's bin
+// is recomputed in FP64: the double-FP32 anchor of an end sample is exact to far below
+// 2^-30 bins, the FP32 coordinate of a last sample that is not an anchor to a few ulps
+// of its block-relative value.
+constexpr float kFirstGuard = 1.0f / (1 << 20);
+__device__ __forceinline__ float last_guard(float v) {
+    return (fabsf(v) + 1.0f) * (1.0f / (1 << 18));
+}
+
+// floor(I + f) - I for a double-FP32 fraction f that lies within rounding of [0, 1)
+__device__ __forceinline__ int frac_floor(float f) { return f >= 1.0f ? 1 : (f < 0.0f ? -1 : 0); }
 
 // The work of one CTA: pixel tile `tile` (kMixThreads * PIX pixels) and electron
 // chunk `chunk` (p.e_chunk electrons) of one variant.  Returns the status bits.
 //
 // The advanced time of a subluminal particle increases strictly along its
-// trajectory (dt_a/dt = 1 - n.beta > 0), so per pixel the grid points that a
-// block of samples reaches form one run (j_done, j_end], where j_end follows
-// from the block's last sample alone, and each of them lies in exactly one
-// step (t_{i-1}, t_i] of Algorithm 2: the first sample i whose coordinate
-// reaches it, found by a bracketed search over the staged block.  Per block a lane
-// evaluates one coordinate per pixel; the grid points of the warp's 32 * PIX
-// pixels are then spread over its 32 lanes (prefix sum of the runs, one grid
-// point per lane and round), each lane finding its step, evaluating the two
-// fields and adding the interpolated value.  Blocks are staged into two
-// alternating shared buffers by asynchronous copies, one block ahead.
-template <int PIX, int ACC>
+// trajectory (dt_a/dt = 1 - n.beta > 0).  Block b owns the steps (t_{i-1}, t_i] of
+// Algorithm 2 that end at samples i0+1 .. i0+B, i.e. from its own anchor (sample i0)
+// to the next block's anchor, so per pixel the grid points it reaches form one run
+// (j_done, floor(u(i0+B))] whose end is the next anchor's coordinate, evaluated once per
+// pixel and block in double-FP32 arithmetic (it is the next block's start as well).
+// Each grid point of the run lies in exactly one of the block's steps: the first
+// sample whose coordinate reaches it.  The grid points of the warp's 32 * PIX pixels
+// are spread over its 32 lanes (prefix sum of the runs, one grid point per lane and
+// round); a lane predicts the step from the linear interpolation between the block's
+// two anchors, confirms it with the two samples around it (or narrows the bracket
+// with regula falsi and bisection when the prediction misses), evaluates the FP32
+// fields at both ends of the step and adds the interpolated value.
+// The bins of the trajectory's first and last samples, where a one-bin rounding flip
+// would add or drop a whole sample (Algorithm 2's half-open interval), are recomputed
+// with the FP64 path's operation order when the mixed value lies within a guard band
+// of an integer.
+template <int PIX, int ACC, int FL>
 __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
-    extern __shared__ __align__(32) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int kSlots = kMixThreads * PIX;
     const int B = p.block;
     const size_t sbytes = stage_bytes(B);
@@ -398,22 +491,27 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     // turn), so the job offsets s_kp are indexed lane-major, wslot + lane * PIX + q; the
     // per-slot data are indexed q-major, wslot + q * 32 + lane, so that a warp's accesses
     // to its own slots are contiguous.
-    __shared__ float4 s_wh[kSlots];                            // slope hi parts (w_x, w_y, w_z)
-    __shared__ int4 s_job[kSlots];                             // block: I, f, v_prev, x_end
-    __shared__ int s_ja[kSlots];                               // block: first grid point
-    __shared__ int s_kp[kSlots];                               // block: job offset (lane-major)
-    __shared__ int2 s_tab[kWarpsMix][kJobTable];               // block: (slot, grid point) of job t
+    __shared__ float4 s_wh[kSlots];                   // slope hi parts (w_x, w_y, w_z)
+    __shared__ int4 s_job[kSlots];                    // block: I, f, x_end
+    __shared__ int s_ja[kSlots];                      // block: first grid point
+    __shared__ int s_kp[kSlots];                      // block: job offset (lane-major)
+    __shared__ int2 s_tab[kWarpsMix][kJobTable];      // block: (slot, grid point) of job t
+    __shared__ __align__(8) uint64_t s_full[kMixStages];   // stage filled (bytes arrived)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wslot = warp * 32 * PIX;
     const float s32 = (float)p.inv_dtu;
-    const float c0_over_R = (float)(kC0 / p.R);
+    const float c0_over_R = (FL & LW_FIELD_VELOCITY) ? (float)(kC0 / p.R) : 0.0f;
     const float inv_sc = (float)(kC0 * p.dt_u);   // direction from slope: n_x = -w_x c0 dt_u
     const int nb = (int)p.n_bins;
     const int64_t pix0 = tile * kSlots;
     unsigned act = 0;
     float wlo[PIX][3];   // slope lo parts of this thread's pixels (its anchors only)
     __syncthreads();   // shared arrays may still be read by the previous unit
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMixStages; ++s) mbar_init(&s_full[s], 1);
+        mbar_init_fence();
+    }
     for (int q = 0; q < PIX; ++q) {
         const int64_t m = pix0 + q * kMixThreads + threadIdx.x;
         double nx = 0.0, ny = 0.0, nz = 1.0;
@@ -435,6 +533,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         wlo[q][1] = wy.lo;
         wlo[q][2] = wz.lo;
     }
+    __syncthreads();   // barriers initialised
     int bits = 0;
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
 
@@ -444,177 +543,178 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         return pix0 + (r / 32) * kMixThreads + w * 32 + r % 32;
     };
     auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
-    // stage block b of electron k into buffer `buf`
+    // blocks with at least one step: ceil((ns1 - 1) / B)
+    const int nbs = (int)((p.ns1 - 2) / B + 1);
+    // field records of a block start 0 or 8 bytes into the buffer's field area: the
+    // bulk copy starts at the 16-byte boundary at or before the block's first record
+    auto field_shift = [&](int64_t k, int b) -> int {
+        return (int)((k * p.ns1 + (int64_t)b * B) & 1) * 8;
+    };
+    // one thread stages block b of electron k into buffer `buf`
     auto issue = [&](int64_t k, int b, int buf) {
         unsigned char* base = smem_raw + buf * sbytes;
-        float4* ss = reinterpret_cast<float4*>(base);
-        float2* sf = reinterpret_cast<float2*>(base + 16 * (size_t)B);
         const int64_t i0 = (int64_t)b * B;
-        const int n = (int)min((int64_t)B, p.ns1 - i0);
-        const float4* src = p.scan + k * p.ns1 + i0;
-        for (int q = threadIdx.x; q < n; q += kMixThreads) cp_async16(ss + q, src + q);
-        // field records of samples i0-1 .. i0+n-1 (3 float2 each); the first block has
-        // no previous sample and leaves that record unset (no step ends at sample 0)
-        const float2* fsrc = reinterpret_cast<const float2*>(p.field + 6 * (k * p.ns1 + i0));
-        for (int q = (b == 0 ? 3 : 0) + threadIdx.x; q < 3 * (n + 1); q += kMixThreads)
-            cp_async8(sf + q, fsrc + (q - 3));
-        cp_async_commit();
-    };
-    // FP32 pairs of block b's anchor (T = (tau_b - t_min)/dt_u, x_b, y_b, z_b): lane l of
-    // every warp splits the anchors of blocks 32c + l at once, one FP64 pass per 32 blocks
-    auto split_anchor = [&](int64_t k, int b, float (&an)[8]) {
-        if (b < p.n_blocks) {
-            const D4 a = p.anchor[k * p.n_blocks + b];
-            const DF T = split_double((a.x - p.t_min) * p.inv_dtu);
-            const DF X = split_double(a.y), Y = split_double(a.z), Z = split_double(a.w);
-            an[0] = T.hi;
-            an[1] = T.lo;
-            an[2] = X.hi;
-            an[3] = X.lo;
-            an[4] = Y.hi;
-            an[5] = Y.lo;
-            an[6] = Z.hi;
-            an[7] = Z.lo;
-        }
+        const int ns = (int)min((int64_t)B, p.ns1 - 1 - i0);   // steps of the block
+        const unsigned scan_bytes = 16u * (unsigned)min((int64_t)B, p.ns1 - i0);
+        const int sh = field_shift(k, b);
+        const unsigned field_bytes = (24u * (unsigned)(ns + 1) + (unsigned)sh + 15u) & ~15u;
+        const int a0 = b == 0 ? 0 : ((b & (kAnchorBatch - 1)) == kAnchorBatch - 1 ? b + 1 : -1);
+        const unsigned anc_bytes =
+            a0 >= 0 ? (unsigned)(sizeof(Anchor) * min(kAnchorBatch, p.n_blocks - a0)) : 0u;
+        fence_proxy_async_smem();   // the buffer's previous contents were read by the CTA
+        mbar_expect_tx(&s_full[buf], scan_bytes + field_bytes + anc_bytes);
+        bulk_g2s(base, p.scan + k * p.ns1 + i0, scan_bytes, &s_full[buf]);
+        bulk_g2s(base + stage_field_off(B),
+                 reinterpret_cast<const unsigned char*>(p.field + 6 * (k * p.ns1 + i0)) - sh,
+                 field_bytes, &s_full[buf]);
+        if (anc_bytes)
+            bulk_g2s(base + stage_anchor_off(B), p.anchor + k * p.n_blocks + a0, anc_bytes,
+                     &s_full[buf]);
     };
 
     const int64_t k0 = chunk * p.e_chunk;
     const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
-    int buf = 0;
-    if (k0 < k1) issue(electron(k0), 0, 0);
-    for (int64_t kk = k0; kk < k1; ++kk) {
-        const int64_t k = electron(kk);
-        const double* ends = p.ends + 8 * k;
-        // per pixel: I = integer anchor of the block, jdone = last grid point reached
-        // so far (absolute), jlast = exact bin of the last sample, vlast = coordinate
-        // (with f) of the block's last sample
-        int I[PIX], jdone[PIX], jlast[PIX];
-        float vlast[PIX];
-        float anc32[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (int q = 0; q < PIX; ++q) {
-            // exact bins of the first and last samples: the half-open interval of
-            // Algorithm 2 makes these the only samples where a one-bin rounding flip
-            // changes the record by a whole sample
-            const int64_t m = (act >> q & 1u) ? pix0 + q * kMixThreads + threadIdx.x : 0;
-            const double nx = p.n_hat[3 * m], ny = p.n_hat[3 * m + 1], nz = p.n_hat[3 * m + 2];
-            jdone[q] = exact_bin(ends, nx, ny, nz, p.t_min, p.inv_dtu);
-            jlast[q] = exact_bin(ends + 4, nx, ny, nz, p.t_min, p.inv_dtu);
-            I[q] = 0;
-            vlast[q] = 0.0f;
+    // ring: the unit's (electron, block) stages in order, kMixStages - 1 in flight ahead;
+    // every thread keeps the bookkeeping, thread 0 issues the copies
+    int64_t iss_kk = k0;   // next stage to issue
+    int iss_b = 0;
+    unsigned pending = 0;   // bit s: buffer s has a copy in flight
+    auto issue_next = [&](int buf) {
+        if (iss_kk < k1) {
+            if (threadIdx.x == 0) issue(electron(iss_kk), iss_b, buf);
+            pending |= 1u << buf;
+            if (++iss_b == nbs) {
+                iss_b = 0;
+                ++iss_kk;
+            }
         }
-        for (int b = 0; b < p.n_blocks; ++b) {
-            const int64_t i0 = (int64_t)b * B;
-            const int n = (int)min((int64_t)B, p.ns1 - i0);
-            cp_async_wait_all();
-            __syncthreads();   // block b staged; every warp is done with block b-1
-            if (b + 1 < p.n_blocks)
-                issue(k, b + 1, buf ^ 1);
-            else if (kk + 1 < k1)
-                issue(electron(kk + 1), 0, buf ^ 1);
-            const unsigned char* base = smem_raw + buf * sbytes;
-            const float4* s_scan = reinterpret_cast<const float4*>(base);
-            const float2* s_field2 = reinterpret_cast<const float2*>(base + 16 * (size_t)B);
-            buf ^= 1;
-            if ((b & 31) == 0) split_anchor(k, b + lane, anc32);
-            float an[8];
+    };
+    for (int st = 0; st + 1 < kMixStages; ++st) issue_next(st);
+    int cur = 0;               // buffer of the block being processed
+    unsigned phase = 0;        // bit s: parity of buffer s's next completion
+    bool timed_out = false;
+    // FP64 bin of an end sample (0 first, 1 last) of electron k for this lane's pixel q,
+    // in the FP64 path's operation order
+    auto end_bin = [&](int64_t k, int q, int which) -> int {
+        const int64_t m = (act >> q & 1u) ? pix0 + q * kMixThreads + threadIdx.x : 0;
+        return exact_bin_rare(p.ends + 8 * k + 4 * which, p.n_hat + 3 * m, p.t_min, p.inv_dtu);
+    };
+    // anchor U = T + W . R_b of pixel q in double-FP32 arithmetic -> I + f
+    auto anchor_of = [&](const float (&an)[8], const float4& wh, int q, int& Iout, float& fout) {
+        const float whc[3] = {wh.x, wh.y, wh.z};
+        float s = an[0], e = an[1];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) an[c] = __shfl_sync(0xffffffffu, anc32[c], b & 31);
-            const bool last_block = (i0 + n == p.ns1);
-            const int lo0 = (b == 0) ? 1 : 0;   // sample 0 ends no step
-            // Grid point j (absolute) of slot sl (q-major) with block data I, f, v0p
-            // (coordinate of sample i0-1), xe (coordinate of the last sample) and slope w:
-            // its step ends at the first sample in [lo0, n-1] whose coordinate reaches
-            // fl(J - f), J = j - I (the last sample if none does, at the trajectory's exact
-            // end).  Search: the bracket (a, b] starts at the block's ends; probes
-            // interpolate the coordinate linearly inside the bracket (regula falsi;
-            // near-linear over a block), bisection after kFalsiProbes, and the final
-            // bracket's two coordinates are the ones the weights need.
-            auto job_core = [&](int sl, int j, int Ib, float f, float v0p, float xe, float4 w) {
-                const float J = (float)(j - Ib);
-                const float tJ = __fsub_rn(J, f);
-                int a = lo0 - 1, hb = n - 1;
-                float xa = lo0 ? coord(w, s32, s_scan[0]) : __fsub_rn(v0p, f);
-                float xb = xe;
-                if (xb < tJ) {   // beyond the FP32 coordinate of the last sample
-                    a = n - 2;
-                    if (a >= 0) xa = coord(w, s32, s_scan[a]);
-                } else {
-                    int probes = 0;
-                    while (hb - a > 1) {
-                        int g = (a + hb) >> 1;
-                        if (probes < kFalsiProbes) {
-                            const float fr = __fdividef(tJ - xa, xb - xa);
-                            const float gf = ceilf(fr * (float)(hb - a));
-                            g = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
-                        }
-                        ++probes;
-                        const float xg = coord(w, s32, s_scan[g]);
-                        if (xg >= tJ) {
-                            hb = g;
-                            xb = xg;
-                        } else {
-                            a = g;
-                            xa = xg;
-                        }
-                    }
+        for (int c = 0; c < 3; ++c) {
+            const float Rh = an[2 + 2 * c], Rl = an[3 + 2 * c];
+            const float pr = __fmul_rn(whc[c], Rh);
+            float pe = fmaf(whc[c], Rh, -pr);
+            pe = fmaf(whc[c], Rl, fmaf(wlo[q][c], Rh, pe));
+            const float s2 = __fadd_rn(s, pr);
+            const float bb = __fsub_rn(s2, s);
+            const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
+            s = s2;
+            e = __fadd_rn(e, __fadd_rn(err, pe));
+        }
+        s = fminf(fmaxf(s, -1.0e9f), 1.0e9f);
+        const float Is = floorf(s);
+        Iout = (int)Is;
+        fout = __fadd_rn(__fsub_rn(s, Is), e);
+    };
+    // FP32 pairs of an anchor (T = (tau_b - t_min)/dt_u, x_b, y_b, z_b); the position's
+    // pairs are stored, T depends on the grid
+    auto split_anchor = [&](const Anchor& a, float (&an)[8]) {
+        const DF T = split_double((a.tau - p.t_min) * p.inv_dtu);
+        an[0] = T.hi;
+        an[1] = T.lo;
+        an[2] = a.x_hi;
+        an[3] = a.x_lo;
+        an[4] = a.y_hi;
+        an[5] = a.y_lo;
+        an[6] = a.z_hi;
+        an[7] = a.z_lo;
+    };
+
+    for (int64_t kk = k0; kk < k1 && !timed_out; ++kk) {
+        const int64_t k = electron(kk);
+        // per pixel: (Is, fs) = the block's start anchor, jdone = last grid point reached
+        // so far (absolute; from the first sample's bin in block 0)
+        int Is[PIX], jdone[PIX];
+        float fs[PIX];
+        float anc32[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        for (int b = 0; b < nbs; ++b) {
+            const int64_t i0 = (int64_t)b * B;
+            const int ns = (int)min((int64_t)B, p.ns1 - 1 - i0);   // steps: (i0+r-1, i0+r], r=1..ns
+            const bool ok = mbar_wait(&s_full[cur], (phase >> cur) & 1u);
+            // every warp is done with the previous block's buffer; a wait that ran out
+            // anywhere stops the whole CTA
+            if (__syncthreads_or(!ok)) {
+                timed_out = true;
+                break;
+            }
+            phase ^= 1u << cur;
+            pending &= ~(1u << cur);
+            issue_next(cur == 0 ? kMixStages - 1 : cur - 1);
+            const unsigned char* base = smem_raw + cur * sbytes;
+            const float4* s_scan = reinterpret_cast<const float4*>(base);
+            const float2* s_field2 =
+                reinterpret_cast<const float2*>(base + stage_field_off(B) + field_shift(k, b));
+            const Anchor* s_anc = reinterpret_cast<const Anchor*>(base + stage_anchor_off(B));
+            cur = cur + 1 == kMixStages ? 0 : cur + 1;
+            // anchors: lane l holds the FP32 pairs of anchor 32c + l (c = batch); block b's
+            // end anchor is b + 1
+            const int ab = b & (kAnchorBatch - 1);
+            if (b == 0) {
+                if (lane < p.n_blocks) split_anchor(s_anc[lane], anc32);
+                float an0[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) an0[c] = __shfl_sync(0xffffffffu, anc32[c], 0);
+#pragma unroll
+                for (int q = 0; q < PIX; ++q) {   // block 0's anchor is sample 0
+                    anchor_of(an0, s_wh[wslot + q * 32 + lane], q, Is[q], fs[q]);
+                    const int fl = frac_floor(fs[q]);
+                    const float fr = fs[q] - (float)fl;
+                    jdone[q] = Is[q] + fl;
+                    if (fr < kFirstGuard || fr > 1.0f - kFirstGuard) jdone[q] = end_bin(k, q, 0);
                 }
-                const int i = hb;
-                const float vi = __fadd_rn(xb, f);
-                const float vp = a >= 0 ? __fadd_rn(xa, f) : v0p;
-                const float a0 = __fsub_rn(J, vp);
-                const float du = __fsub_rn(vi, vp);
-                PixelConst pc;
-                pc.nx = -w.x * inv_sc;
-                pc.ny = -w.y * inv_sc;
-                pc.omnz = w.z * inv_sc;
-                pc.nz = 1.0f - pc.omnz;
-                float Fb[3], Fa[3];
-                field_fp32(pc, s_field2 + 3 * i, p.flags, c0_over_R, Fb);
-                field_fp32(pc, s_field2 + 3 * (i + 1), p.flags, c0_over_R, Fa);
-                const float wb = du > 0.0f ? __fdividef(a0, du) : 0.0f;
-                const float wa = 1.0f - wb;
-                deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, fmaf(Fb[0], wa, Fa[0] * wb),
-                              fmaf(Fb[1], wa, Fa[1] * wb), fmaf(Fb[2], wa, Fa[2] * wb));
-            };
-            // a job handed to the warp: the slot's block data from shared memory
-            auto job = [&](int sl, int j) {
-                const int4 jb = s_job[sl];
-                job_core(sl, j, jb.x, __int_as_float(jb.y), __int_as_float(jb.z),
-                         __int_as_float(jb.w), s_wh[sl]);
-            };
+            }
+            const bool end_anchor = i0 + B <= p.ns1 - 1;   // the block ends at anchor b + 1
+            const bool traj_end = i0 + ns == p.ns1 - 1;    // ... at the trajectory's last sample
+            float ane[8];
+            if (end_anchor) {
+                if (ab == kAnchorBatch - 1) {   // the next batch was staged with this block
+                    if (lane < p.n_blocks - (b + 1)) split_anchor(s_anc[lane], anc32);
+                }
+                const int src = ab == kAnchorBatch - 1 ? 0 : ab + 1;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) ane[c] = __shfl_sync(0xffffffffu, anc32[c], src);
+            }
             int K[PIX], big[PIX], JA[PIX];
             int tot = 0;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
                 const int sl = wslot + q * 32 + lane;
-                // anchor U = T + W . R_b in double-FP32 arithmetic -> I + f
                 const float4 wh = s_wh[sl];
-                const float whc[3] = {wh.x, wh.y, wh.z};
-                const float wlc[3] = {wlo[q][0], wlo[q][1], wlo[q][2]};
-                float s = an[0], e = an[1];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float Rh = an[2 + 2 * c], Rl = an[3 + 2 * c];
-                    const float pr = __fmul_rn(whc[c], Rh);
-                    float pe = fmaf(whc[c], Rh, -pr);
-                    pe = fmaf(whc[c], Rl, fmaf(wlc[c], Rh, pe));
-                    const float s2 = __fadd_rn(s, pr);
-                    const float bb = __fsub_rn(s2, s);
-                    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)),
-                                                __fsub_rn(pr, bb));
-                    s = s2;
-                    e = __fadd_rn(e, __fadd_rn(err, pe));
+                int Ie = 0, jend;
+                float fe = 0.0f, xe;
+                if (end_anchor) {
+                    anchor_of(ane, wh, q, Ie, fe);
+                    const int fl = frac_floor(fe);
+                    jend = Ie + fl;
+                    if (traj_end) {
+                        const float fr = fe - (float)fl;
+                        if (fr < kFirstGuard || fr > 1.0f - kFirstGuard) jend = end_bin(k, q, 1);
+                    }
+                    // end coordinate relative to the start anchor, without its fraction
+                    xe = __fadd_rn((float)(Ie - Is[q]), __fsub_rn(fe, fs[q]));
+                } else {   // the trajectory's last sample, inside this block
+                    xe = coord(wh, s32, s_scan[ns]);
+                    const float v = __fadd_rn(xe, fs[q]);
+                    const float fv = floorf(v), d = v - fv, gd = last_guard(v);
+                    jend = Is[q] + (int)fv;
+                    if (d < gd || d > 1.0f - gd || !(fabsf(v) < 1.0e9f)) jend = end_bin(k, q, 1);
                 }
-                s = fminf(fmaxf(s, -1.0e9f), 1.0e9f);
-                const float Is = floorf(s);
-                const int Inew = (int)Is;
-                const float f = __fadd_rn(__fsub_rn(s, Is), e);
-                const float v0p = __fadd_rn(vlast[q], (float)(I[q] - Inew));   // sample i0-1
-                I[q] = Inew;
-                const float xe = coord(wh, s32, s_scan[n - 1]);
-                const int jend = last_block ? jlast[q] : Inew + last_point(xe, f);
                 int ja = jdone[q] + 1, jz = jend, kq = 0;
-                if ((act >> q & 1u) && jz >= ja && n > lo0) {
+                if ((act >> q & 1u) && jz >= ja) {
                     if (ja < 0) {
                         ja = 0;
                         bits |= LW_ST_CLIP;
@@ -626,15 +726,87 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     kq = max(0, jz - ja + 1);
                 }
                 if (jend > jdone[q]) jdone[q] = jend;
-                vlast[q] = __fadd_rn(xe, f);
-                s_job[sl] = make_int4(Inew, __float_as_int(f), __float_as_int(v0p),
-                                      __float_as_int(xe));
+                s_job[sl] = make_int4(Is[q], __float_as_int(fs[q]), __float_as_int(xe), 0);
                 s_ja[sl] = ja;
                 JA[q] = ja;
                 big[q] = kq > kMaxWarpJobs ? kq : 0;
                 K[q] = kq > kMaxWarpJobs ? 0 : kq;
                 tot += K[q];
+                Is[q] = Ie;
+                fs[q] = fe;
             }
+            // Grid point j (absolute) of slot sl with block data I, f, xe (coordinate of the
+            // block's last sample relative to the anchor) and slope w: its step ends at the
+            // first sample r in 1..ns whose coordinate reaches fl(J - f), J = j - I (the
+            // last one if none does).  x(0) = 0 (the anchor) and x(ns) = xe bracket it.
+            auto job = [&](int sl, int j) {
+                const int4 jb = s_job[sl];
+                const float4 w = s_wh[sl];
+                const float f = __int_as_float(jb.y), xe = __int_as_float(jb.z);
+                const float tJ = __fsub_rn((float)(j - jb.x), f);
+                int a = 0, hb = ns;
+                float xa = 0.0f, xb = xe;
+                if (xe < tJ) {   // beyond the FP32 coordinate of the last sample: last step
+                    a = ns - 1;
+                    xa = a > 0 ? coord(w, s32, s_scan[a]) : 0.0f;
+                } else if (ns > 1) {
+                    // predicted step end g: the interpolated crossing between the anchors
+                    const float fr = __fdividef(tJ, xe);
+                    int g = (int)ceilf(fr * (float)ns);
+                    g = min(max(g, 1), ns);
+                    const float xl = g > 1 ? coord(w, s32, s_scan[g - 1]) : 0.0f;
+                    const float xg = g < ns ? coord(w, s32, s_scan[g]) : xe;
+                    if (xg < tJ) {
+                        a = g;
+                        xa = xg;
+                    } else if (xl >= tJ) {
+                        if (g > 1) {
+                            hb = g - 1;
+                            xb = xl;
+                        } else {   // at or before the anchor (FP32 rounding): first step
+                            hb = 1;
+                            xb = xg;
+                        }
+                    } else {
+                        a = g - 1;
+                        xa = xl;
+                        hb = g;
+                        xb = xg;
+                    }
+                    int probes = 0;
+                    while (hb - a > 1) {   // the prediction missed: narrow the bracket
+                        int g2 = (a + hb) >> 1;
+                        if (probes < kFalsiProbes) {
+                            const float r = __fdividef(tJ - xa, xb - xa);
+                            const float gf = ceilf(r * (float)(hb - a));
+                            g2 = a + (int)fminf(fmaxf(gf, 1.0f), (float)(hb - a - 1));
+                        }
+                        ++probes;
+                        const float xg2 = coord(w, s32, s_scan[g2]);
+                        if (xg2 >= tJ) {
+                            hb = g2;
+                            xb = xg2;
+                        } else {
+                            a = g2;
+                            xa = xg2;
+                        }
+                    }
+                }
+                // step (a, hb]: field records a and hb (record r = sample i0 + r)
+                PixelConst pc;
+                pc.nx = -w.x * inv_sc;
+                pc.ny = -w.y * inv_sc;
+                pc.omnz = w.z * inv_sc;
+                pc.nz = 1.0f - pc.omnz;
+                float Fb[3], Fa[3];
+                field_fp32<FL>(pc, s_field2 + 3 * a, c0_over_R, Fb);
+                field_fp32<FL>(pc, s_field2 + 3 * hb, c0_over_R, Fa);
+                const float du = __fsub_rn(xb, xa);
+                const float wb = du > 0.0f ? __fdividef(__fsub_rn(tJ, xa), du) : 0.0f;
+                const float wa = 1.0f - wb;
+                deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, fmaf(Fb[0], wa, Fa[0] * wb),
+                              fmaf(Fb[1], wa, Fa[1] * wb), fmaf(Fb[2], wa, Fa[2] * wb));
+            };
             // the warp's grid points: prefix sum of the runs over the warp's slots, and the
             // first kJobTable of them listed as (slot, grid point) by their owners
             int incl = tot;
@@ -684,7 +856,16 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             __syncwarp();   // s_job / s_kp are rewritten for the next block
         }
     }
-    cp_async_wait_all();
+    if (timed_out) {
+        bits |= LW_ST_TIMEOUT;
+        // copies may still be in flight into the ring: wait for each one, again with a
+        // bounded wait, before the CTA leaves
+        for (int s = 0; s < kMixStages; ++s)
+            if (pending >> s & 1u) mbar_wait(&s_full[s], (phase >> s) & 1u);
+    }
+    __syncthreads();   // every stage consumed; the barriers can be retired
+    if (threadIdx.x == 0)
+        for (int s = 0; s < kMixStages; ++s) mbar_inval(&s_full[s]);
     return bits;
 }
 
@@ -928,9 +1109,9 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
     block_status_or(p.status, bits);
 }
 
-template <int PIX, int ACC>
+template <int PIX, int ACC, int FL>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
-    const int bits = mixed_cta<PIX, ACC>(p, blockIdx.x, blockIdx.y);
+    const int bits = mixed_cta<PIX, ACC, FL>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
 }
 
@@ -949,7 +1130,7 @@ struct BatchUnit {
 constexpr int kBatchMaxItems = 256;
 __constant__ DepositArgs c_batch_vars[kBatchMaxItems];
 
-template <int PIX, int ACC>
+template <int PIX, int ACC, int FL>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     deposit_batched_kernel(const BatchUnit* __restrict__ units, int n_units, int* counter) {
     __shared__ int s_unit;
@@ -960,7 +1141,7 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
         if (u >= n_units) break;
         const BatchUnit un = units[u];
         const DepositArgs& p = c_batch_vars[un.variant];
-        const int bits = mixed_cta<PIX, ACC>(p, un.tile, un.chunk);
+        const int bits = mixed_cta<PIX, ACC, FL>(p, un.tile, un.chunk);
         block_status_or(p.status, bits);
     }
 }
@@ -981,6 +1162,31 @@ __global__ void zero_records_kernel(const DepositArgs* __restrict__ vars, int wo
     } else {
         for (int64_t i = i0; i < n; i += stride) rec[i] = 0.0f;
     }
+}
+
+// Kernel instances by accumulation form and field terms (LW_FIELD_* mask 1, 2 or 3).
+using MixedKernel = void (*)(DepositArgs);
+using BatchedKernel = void (*)(const BatchUnit*, int, int*);
+template <int ACC>
+MixedKernel mixed_kernel_fl(uint32_t fl) {
+    return fl == 1 ? deposit_mixed_kernel<kMixPix, ACC, 1>
+           : fl == 2 ? deposit_mixed_kernel<kMixPix, ACC, 2> : deposit_mixed_kernel<kMixPix, ACC, 3>;
+}
+MixedKernel mixed_kernel(int acc, uint32_t fl) {
+    return acc == kAccKahan ? mixed_kernel_fl<kAccKahan>(fl)
+           : acc == kAccF32 ? mixed_kernel_fl<kAccF32>(fl)
+           : acc == kAccF32X4 ? mixed_kernel_fl<kAccF32X4>(fl) : mixed_kernel_fl<kAccF64>(fl);
+}
+template <int ACC>
+BatchedKernel batched_kernel_fl(uint32_t fl) {
+    return fl == 1 ? deposit_batched_kernel<kMixPix, ACC, 1>
+           : fl == 2 ? deposit_batched_kernel<kMixPix, ACC, 2>
+                     : deposit_batched_kernel<kMixPix, ACC, 3>;
+}
+BatchedKernel batched_kernel(int acc, uint32_t fl) {
+    return acc == kAccKahan ? batched_kernel_fl<kAccKahan>(fl)
+           : acc == kAccF32 ? batched_kernel_fl<kAccF32>(fl)
+           : acc == kAccF32X4 ? batched_kernel_fl<kAccF32X4>(fl) : batched_kernel_fl<kAccF64>(fl);
 }
 
 }  // namespace
@@ -1018,7 +1224,7 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     a.bdot = traj->beta_dot;
     a.scan = static_cast<const float4*>(traj->scan);
     a.field = static_cast<const float*>(traj->field);
-    a.anchor = reinterpret_cast<const D4*>(traj->anchor);
+    a.anchor = reinterpret_cast<const Anchor*>(traj->anchor);
     a.block = traj->block;
     a.n_blocks = traj->n_blocks;
     a.input_status = traj->input_status;
@@ -1044,18 +1250,19 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     }
     constexpr int PIX = kMixPix;
     const int64_t tiles = (det->n_pix + kMixThreads * PIX - 1) / (kMixThreads * PIX);
-    // one electron per CTA row (as few as the grid's y limit allows), CTAs dispatched
-    // tile-fastest: the electrons in flight are consecutive in arrival order, so the
-    // record bins they update stay few enough to be served from L2
-    a.e_chunk = (int)std::max<int64_t>(1, (traj->n_e + 65534) / 65535);
+    // a few consecutive electrons (in arrival order) per CTA row -- enough rows for
+    // about eight waves of resident CTAs -- dispatched tile-fastest: the electrons in
+    // flight stay consecutive in arrival order, so the record bins they update are few
+    // enough to be served from L2, and each CTA's pixel set-up serves several electrons
+    const int64_t rows_wanted = (int64_t)kSms * kMixMinBlocks * 8 / std::max<int64_t>(1, tiles);
+    int64_t ec = traj->n_e / std::max<int64_t>(1, rows_wanted);
+    ec = std::min<int64_t>(std::max<int64_t>(ec, 1),
+                           precision == LW_MIXED_F32X4 ? kMixMaxChunkX4 : kMixMaxChunk);
+    a.e_chunk = (int)std::max<int64_t>(ec, (traj->n_e + 65534) / 65535);
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
-    const size_t smem = 2 * stage_bytes(traj->block);   // double-buffered staging
+    const size_t smem = kMixStages * stage_bytes(traj->block);   // staging ring
     // static tables + double-buffered staging exceed the 48 KB default: opt in
-    const int acc = acc_of(precision);
-    auto kern = acc == kAccKahan ? deposit_mixed_kernel<PIX, kAccKahan>
-                : acc == kAccF32 ? deposit_mixed_kernel<PIX, kAccF32>
-                : acc == kAccF32X4 ? deposit_mixed_kernel<PIX, kAccF32X4>
-                                   : deposit_mixed_kernel<PIX, kAccF64>;
+    const MixedKernel kern = mixed_kernel(acc_of(precision), field_flags);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return LW_ECUDA;
@@ -1125,7 +1332,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
         a.t_per_e = it.traj->t_per_electron;
         a.scan = static_cast<const float4*>(it.traj->scan);
         a.field = static_cast<const float*>(it.traj->field);
-        a.anchor = reinterpret_cast<const D4*>(it.traj->anchor);
+        a.anchor = reinterpret_cast<const Anchor*>(it.traj->anchor);
         a.block = it.traj->block;
         a.n_blocks = it.traj->n_blocks;
         a.input_status = it.traj->input_status;
@@ -1199,7 +1406,9 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
     plan->n_items = n_items;
     plan->n_units = (int32_t)sorted.size();
     plan->precision = precision;
-    plan->smem_bytes = (int32_t)(2 * stage_bytes(max_block));
+    plan->smem_bytes = (int32_t)(kMixStages * stage_bytes(max_block));
+    plan->field_flags = (int32_t)field_flags;
+    plan->reserved = 0;
     plan->offsets[0] = (int64_t)o_counter;
     plan->offsets[1] = (int64_t)o_vars;
     plan->offsets[2] = (int64_t)o_units;
@@ -1223,11 +1432,8 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
     if (cudaMemcpyToSymbolAsync(c_batch_vars, vars, sizeof(DepositArgs) * (size_t)plan->n_items,
                                 0, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return LW_ECUDA;
-    const int acc = acc_of(plan->precision);
-    auto kern = acc == kAccKahan ? deposit_batched_kernel<PIX, kAccKahan>
-                : acc == kAccF32 ? deposit_batched_kernel<PIX, kAccF32>
-                : acc == kAccF32X4 ? deposit_batched_kernel<PIX, kAccF32X4>
-                                   : deposit_batched_kernel<PIX, kAccF64>;
+    if (plan->field_flags < 1 || plan->field_flags > 3) return LW_EINVAL;
+    const BatchedKernel kern = batched_kernel(acc_of(plan->precision), (uint32_t)plan->field_flags);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              plan->smem_bytes) != cudaSuccess)
         return LW_ECUDA;

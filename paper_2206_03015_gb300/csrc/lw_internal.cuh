@@ -16,9 +16,12 @@ constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kSms = 152;   // GB300 streaming multiprocessors (2 dies x 76)
 
-// 32-byte aligned quadruple of doubles (anchor records of the mixed section)
-struct alignas(32) D4 {
-    double x, y, z, w;
+// Anchor record of the mixed section (32 bytes): the block's light-front time
+// tau_b = t_b - z_b/c0 in FP64 and its position as unevaluated FP32 pairs (hi, lo),
+// hi = fl32(x), lo = fl32(x - hi), per component.
+struct alignas(32) Anchor {
+    double tau;
+    float x_hi, x_lo, y_hi, y_lo, z_hi, z_lo;
 };
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }

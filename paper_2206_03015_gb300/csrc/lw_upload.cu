@@ -6,8 +6,8 @@
 //   MIXED  per sample a float4 (tau - tau_b, x - x_b, y - y_b, z - z_b) with the
 //          light-front time tau = t - z/c0 taken relative to the first sample of
 //          the sample's anchoring block, six floats of field data
-//          (beta_x, beta_y, 1 - beta_z, beta_dot), and per block the FP64 anchor
-//          (tau_b, x_b, y_b, z_b).  Subtracting the anchor in FP64 keeps the FP32
+//          (beta_x, beta_y, 1 - beta_z, beta_dot), and per block the anchor
+//          (tau_b in FP64, x_b, y_b, z_b as FP32 pairs).  Subtracting the anchor in FP64 keeps the FP32
 //          numbers small, so the FP32 part of the bin coordinate stays accurate.
 // lw_grid_bounds evaluates Eqs. (tu_min) and (tu_max).
 #include <math.h>
@@ -56,7 +56,7 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
         L.field = off;
         off = align256(off + sizeof(float) * 6 * (size_t)(n_e * ns1));
         L.anchor = off;
-        off = align256(off + sizeof(D4) * (size_t)(n_e * L.n_blocks));
+        off = align256(off + sizeof(Anchor) * (size_t)(n_e * L.n_blocks));
     }
     L.order = off;
     off = align256(off + sizeof(int32_t) * (size_t)n_e);
@@ -71,7 +71,7 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
 // finite values, |beta| < 1 (evaluated as ((bx*bx + by*by) + bz*bz) < 1),
 // strictly increasing lab time, and with `check_steps` consecutive samples
 // closer than c0 dt (LW_ST_STEP otherwise) -- and, when `scan` is non-null, the mixed
-// section (block-relative float4, six field floats, per-block FP64 anchor).
+// section (block-relative float4, six field floats, per-block anchor).
 // The [sample][3] inputs and the [sample][6] field output are moved through
 // shared memory so that every global access is a contiguous run.
 constexpr int kPrepThreads = 256;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
                    int ns1, int block_shift, int n_blocks, float4* __restrict__ scan,
-                   float* __restrict__ field, D4* __restrict__ anchor, int check_steps,
+                   float* __restrict__ field, Anchor* __restrict__ anchor, int check_steps,
                    int32_t* __restrict__ status) {
     __shared__ double s_in[3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
     __shared__ float s_out[6 * kPrepThreads];       // field records of the chunk
@@ -159,7 +159,17 @@ __global__ void __launch_bounds__(kPrepThreads)
                 s_out[6 * l + 3] = to_float(a0);
                 s_out[6 * l + 4] = to_float(a1);
                 s_out[6 * l + 5] = to_float(a2);
-                if (i == ib) anchor[k * n_blocks + (i >> block_shift)] = D4{taub, xb, yb, zb};
+                if (i == ib) {   // position as FP32 pairs: hi = fl32(x), lo = fl32(x - hi)
+                    Anchor an;
+                    an.tau = taub;
+                    an.x_hi = __double2float_rn(xb);
+                    an.x_lo = __double2float_rn(xb - (double)an.x_hi);
+                    an.y_hi = __double2float_rn(yb);
+                    an.y_lo = __double2float_rn(yb - (double)an.y_hi);
+                    an.z_hi = __double2float_rn(zb);
+                    an.z_lo = __double2float_rn(zb - (double)an.z_hi);
+                    anchor[k * n_blocks + (i >> block_shift)] = an;
+                }
             }
         }
         if (scan) {
@@ -387,11 +397,11 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
     v.ends = ends;
     float4* scan = nullptr;
     float* field = nullptr;
-    D4* anchor = nullptr;
+    Anchor* anchor = nullptr;
     if (sections & LW_SECTION_MIXED) {
         scan = reinterpret_cast<float4*>(base + L.scan);
         field = reinterpret_cast<float*>(base + L.field);
-        anchor = reinterpret_cast<D4*>(base + L.anchor);
+        anchor = reinterpret_cast<Anchor*>(base + L.anchor);
         v.scan = scan;
         v.field = field;
         v.anchor = reinterpret_cast<const double*>(anchor);

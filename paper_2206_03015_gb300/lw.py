@@ -22,6 +22,7 @@ LW_OK, LW_EINVAL, LW_ESIZE, LW_ECUDA, LW_EUNSUPPORTED, LW_ETIMEOUT = 0, -1, -2, 
 LW_FP64, LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32, LW_MIXED_F32X4 = 0, 1, 2, 3, 4
 LW_FIELD_ACCEL, LW_FIELD_VELOCITY = 1, 2
 LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER, LW_ST_STEP = 1, 2, 4, 8, 16, 32
+LW_ST_TIMEOUT = 64
 LW_SECTION_FP64, LW_SECTION_MIXED = 1, 2
 
 Q_E = 1.602176634e-19
@@ -57,6 +58,7 @@ class lw_traj(ctypes.Structure):
 class lw_batch(ctypes.Structure):
     _fields_ = [("ws", ctypes.c_void_p), ("n_items", ctypes.c_int32), ("n_units", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("field_flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("offsets", ctypes.c_int64 * 3)]
 
 
