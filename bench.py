@@ -150,6 +150,60 @@ def grid_points_reached(t, r, det, grid, chunk=256):
     return total
 
 
+# Work of one mixed deposit launch (Algorithm 2 as the kernel evaluates it), per unit:
+#   per grid point reached: two FP32 fields (29 flops each), the interpolation of three
+#   components (9), its weight (5) and the two sample coordinates that bracket the step
+#   (7 each): 86 flops; the two staged samples it reads: 2 x (16 B coordinate data + 24 B
+#   field data) = 80 B of shared memory; its update of the record: one L2 reduction
+#   (LW_MIXED_F32X4: x, y, z in one 16-byte vector) or three (the other records);
+#   per pixel and block of samples: the double-FP32 anchor, 47 flops;
+#   per launch from HBM: the mixed trajectory section once (40 B per sample, 32 B per
+#   anchor) and the record once (three components per pixel and grid point).
+FLOPS_PER_POINT = 86
+FLOPS_PER_PIXEL_BLOCK = 47
+SMEM_BYTES_PER_POINT = 80
+
+
+def deposit_work(n_e, n_s, n_pix, n_bins, block, n_points, precision):
+    """Algorithmic work of one mixed deposit launch (see the model above)."""
+    from paper_2206_03015_gb300 import lw
+    ns1 = n_s + 1
+    n_blocks = -(-ns1 // block)
+    step_blocks = -(-(ns1 - 1) // block)          # blocks that hold steps
+    rec_word = 8 if precision in (lw.LW_MIXED, lw.LW_MIXED_KAHAN) else 4
+    return {
+        "grid_points": n_points,
+        "pixel_blocks": n_pix * n_e * step_blocks,
+        "hbm_bytes": n_e * (ns1 * (16 + 24) + n_blocks * 32) + n_pix * 3 * n_bins * rec_word,
+        "l2_ops": n_points * (1 if precision == lw.LW_MIXED_F32X4 else 3),
+        "fp32_flops": n_points * FLOPS_PER_POINT + n_pix * n_e * step_blocks * FLOPS_PER_PIXEL_BLOCK,
+        "smem_bytes": n_points * SMEM_BYTES_PER_POINT,
+    }
+
+
+def deposit_roofline(work, kernel_ms, pipe_peaks, hbm_gbs, traffic=None):
+    """Each bound's achieved rate (work / kernel time), peak and fraction; the binding one
+    (largest fraction) is the headline."""
+    t = kernel_ms * 1e-3
+    l2 = pipe_peaks["red_v4f32_lines"]["ops_per_s"]
+    bounds = {
+        "hbm": {"achieved": work["hbm_bytes"] / t / 1e9, "peak": hbm_gbs, "unit": "GB/s"},
+        "l2_red": {"achieved": work["l2_ops"] / t / 1e9, "peak": l2 / 1e9, "unit": "Gop/s"},
+        "fp32": {"achieved": work["fp32_flops"] / t / 1e12,
+                 "peak": pipe_peaks["fma_f32"]["flops"] / 1e12, "unit": "TFLOP/s"},
+        "smem": {"achieved": work["smem_bytes"] / t / 1e9,
+                 "peak": pipe_peaks["lds_v4"]["bytes_per_s"] / 1e9, "unit": "GB/s"},
+    }
+    for b in bounds.values():
+        b["frac"] = b["achieved"] / b["peak"]
+    bound = max(bounds, key=lambda k: bounds[k]["frac"])
+    out = {"bound": bound, "achieved": bounds[bound]["achieved"], "peak": bounds[bound]["peak"],
+           "unit": bounds[bound]["unit"], "frac": bounds[bound]["frac"],
+           "traffic": traffic, "kernel": "deposit_mixed_kernel", "kernel_ms": kernel_ms,
+           "bounds": bounds, "work": work}
+    return out
+
+
 # ----------------------------------------------------------------------------- workload
 
 def shard_pixels(n_pix, rank, world, shard="pixels"):
@@ -266,6 +320,8 @@ def run_ours(args, rank, world, dist):
             ms = float(x.item())
         return ms, clocks
 
+    from paper_2206_03015_gb300 import peaks
+    pipe_peaks = peaks.measure(dev)   # rates of the deposit's pipes on this GPU
     sampler = ClockSampler(dev.index)
     ms_m, clocks = timed_loop(step_mixed, args.steps, args.warmup, sampler)
     ms_step = ms_m / args.steps
@@ -293,33 +349,23 @@ def run_ours(args, rank, world, dist):
                    "deposits_per_step_job": n_job,
                    "generation_s": round(t_gen, 1)},
     }
-    # roofline of the dominant kernel (mixed deposit) against HBM: the algorithmic bytes
-    # of one launch are its inputs read once (mixed trajectory section: float4 scan +
-    # six field floats per sample, one FP64 anchor per block) and the record written
-    # once; its updates are 3 atomics per grid point reached (counted from the exact
-    # bins of each (pixel, electron) trajectory's first and last sample)
+    # roofline of the dominant kernel (the mixed deposit): the work of one launch by the
+    # model in deposit_work(), against pipe peaks measured on this GPU just before the
+    # timed region (HBM: the measured copy bandwidth)
     hbm_peak, peak_src = 6800.0, "fallback"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             hbm_peak, peak_src = float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
         pass
-    ns1 = tr.n_s + 1
-    n_blocks = -(-ns1 // args.block)
-    traj_bytes = tr.n_e * (ns1 * (16 + 24) + n_blocks * 32)
-    rec_bytes = w.n_pix * 3 * w.n_bins * rec_m.element_size()
-    alg_bytes = traj_bytes + rec_bytes
-    achieved = alg_bytes / (dep_ms * 1e-3) / 1e9
+    n_points = grid_points_reached(t_d, r_d, det, grid)
+    work = deposit_work(tr.n_e, tr.n_s, w.n_pix, w.n_bins, args.block, n_points, MIX)
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2206_03015_gb300", "csrc",
                                                  "lw_deposit.cu"))
-    n_points = grid_points_reached(t_d, r_d, det, grid)
-    result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                          "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                          "kernel": "deposit_mixed_kernel", "kernel_ms": dep_ms,
-                          "algorithmic_bytes": alg_bytes,
-                          "grid_points": n_points,
-                          "atomics_per_s": 3.0 * n_points / (dep_ms * 1e-3)}
+    result["roofline"] = deposit_roofline(work, dep_ms, pipe_peaks, hbm_peak, traffic)
+    result["roofline"]["peak_source"] = (f"{peak_src} HBM copy (MEASURED_PEAKS.json hbm_gbs); "
+                                         "L2 reductions, FP32 FMA and shared loads measured "
+                                         "in this run (paper_2206_03015_gb300/peaks)")
     result["clocks"] = clocks
     # the other mixed record beside it (FP64 record when the FP32 one is timed)
     if MIX != lw.LW_MIXED:
@@ -681,7 +727,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mixed", default="f32", choices=["f32", "x4", "f64"],
+    ap.add_argument("--mixed", default="x4", choices=["f32", "x4", "f64"],
                     help="record of the timed mixed path: FP32 (LW_MIXED_F32), FP32 interleaved "
                          "(LW_MIXED_F32X4) or FP64 (LW_MIXED)")
     ap.add_argument("--e2e-chunks", type=int, default=6)

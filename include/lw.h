@@ -95,8 +95,17 @@ enum {
     LW_ST_STEP = 32,       /* two consecutive samples at least c0 (t_i - t_(i-1)) apart
                               (checked by uploads with the FP64 section): the advanced time
                               may decrease for some direction */
-    LW_ST_TIMEOUT = 64     /* a kernel's bounded wait for its staged input ran out (the
+    LW_ST_TIMEOUT = 64,    /* a kernel's bounded wait for its staged input ran out (the
                               record is incomplete) */
+    LW_ST_PRECISION = 128  /* mixed deposits: the estimated FP32 error of some tile's
+                              contributions (interpolation weights from FP32 coordinates,
+                              FP32 Doppler factors) exceeds 2^-11 of their root mean square.
+                              The estimate is conservative: on the cases it was calibrated on,
+                              every mixed spectrum more than 1e-4 (relative L2) from the FP64
+                              one raised it, and none within 2.5e-5 of it did.  Typical
+                              causes: fields that change by a large fraction across a step
+                              (an observer inside a synchrotron cone sampled coarsely), or
+                              velocities far from the z axis.  LW_FP64 has no such limit */
 };
 
 /* Which device sections lw_trajectories_upload builds (bit mask). */

@@ -457,6 +457,35 @@ __device__ __forceinline__ float last_guard(float v) {
     return (fabsf(v) + 1.0f) * (1.0f / (1 << 18));
 }
 
+// Precision check of the mixed deposit.  An FP32 block-relative coordinate carries an
+// absolute error of about an ulp of the terms it sums; the interpolation weight
+// (t_J - x_a)/(x_b - x_a) of a step of du bins then errs by about
+// kCoordEps (|x_a| + |x_b| + |t_J|) / du, and the deposited value by that fraction of the
+// field's change across the step; the fields themselves carry the rounding of their
+// Doppler factor.  A separate launch of the same CTA routine (CHECK, which deposits
+// nothing) evaluates a sample of the units -- every kCheckStride-th electron chunk -- and
+// adds up the squares of these estimates and of the values; a unit whose root-mean-square
+// ratio exceeds kPrecisionTol sets LW_ST_PRECISION.  The deposit itself carries none of
+// this arithmetic.
+constexpr float kCoordEps = 1.0f / (1 << 23);
+constexpr int kCheckStride = 64;
+constexpr float kPrecisionTol = 1.0f / (1 << 11);
+
+// Sum of the sizes of the terms of coord(): its rounding is about an ulp of this.
+__device__ __forceinline__ float coord_mag(float4 w, float s, float4 sc) {
+    return fabsf(s * sc.x) + fabsf(w.x * sc.y) + fabsf(w.y * sc.z) + fabsf(w.z * sc.w);
+}
+
+// Relative error of an FP32 field through its Doppler factor: D sums terms of size
+// (1 - n_z) + n_z (1 - beta_z) + |n_x beta_x| + |n_y beta_y|, each rounded to about an ulp,
+// and enters the field as D^-3.
+__device__ __forceinline__ float fd_rel(const PixelConst& pc, const float2* __restrict__ f) {
+    const float2 f01 = f[0], f23 = f[1];
+    const float D = fmaf(-pc.ny, f01.y, fmaf(-pc.nx, f01.x, fmaf(pc.nz, f23.x, pc.omnz)));
+    const float mag = fabsf(pc.nx * f01.x) + fabsf(pc.ny * f01.y) + pc.omnz + pc.nz * f23.x;
+    return D > 0.0f ? 3.0f * kCoordEps * mag / D : 0.0f;
+}
+
 // floor(I + f) - I for a double-FP32 fraction f that lies within rounding of [0, 1)
 __device__ __forceinline__ int frac_floor(float f) { return f >= 1.0f ? 1 : (f < 0.0f ? -1 : 0); }
 
@@ -480,7 +509,7 @@ __device__ __forceinline__ int frac_floor(float f) { return f >= 1.0f ? 1 : (f <
 // would add or drop a whole sample (Algorithm 2's half-open interval), are recomputed
 // with the FP64 path's operation order when the mixed value lies within a guard band
 // of an integer.
-template <int PIX, int ACC, int FL>
+template <int PIX, int ACC, int FL, bool CHECK>
 __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int64_t chunk) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int kSlots = kMixThreads * PIX;
@@ -536,6 +565,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     __syncthreads();   // barriers initialised
     int bits = 0;
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
+    float err2 = 0.0f, val2 = 0.0f;   // CHECK: squared error estimates and squared values
 
     // pixel (global index) of q-major slot `sl`
     auto slot_pixel = [&](int sl) -> int64_t {
@@ -804,8 +834,33 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 const float du = __fsub_rn(xb, xa);
                 const float wb = du > 0.0f ? __fdividef(__fsub_rn(tJ, xa), du) : 0.0f;
                 const float wa = 1.0f - wb;
-                deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, fmaf(Fb[0], wa, Fa[0] * wb),
-                              fmaf(Fb[1], wa, Fa[1] * wb), fmaf(Fb[2], wa, Fa[2] * wb));
+                const float v0 = fmaf(Fb[0], wa, Fa[0] * wb), v1 = fmaf(Fb[1], wa, Fa[1] * wb);
+                const float v2 = fmaf(Fb[2], wa, Fa[2] * wb);
+                if (CHECK) {   // error estimate instead of the deposit
+                    if (!(du > 0.0f)) return;
+                    // the weight's: the field's change times the weight's rounding, from the
+                    // sizes of the terms the two coordinates sum (the anchor's is exact, the
+                    // next anchor's a double-FP32 difference)
+                    const float ma = a > 0 ? coord_mag(w, s32, s_scan[a]) : 0.0f;
+                    const float mb = (hb < ns || !end_anchor) ? coord_mag(w, s32, s_scan[hb])
+                                                              : fabsf(xb);
+                    const float dw = kCoordEps * (ma + mb + fabsf(tJ)) / du;
+                    float e = dw * (fabsf(Fa[0] - Fb[0]) + fabsf(Fa[1] - Fb[1]) +
+                                    fabsf(Fa[2] - Fb[2]));
+                    // the fields': D in FP32 loses the terms' size over D, three times in D^3
+                    e = fmaf(fd_rel(pc, s_field2 + 3 * a) * wa,
+                             fabsf(Fb[0]) + fabsf(Fb[1]) + fabsf(Fb[2]), e);
+                    e = fmaf(fd_rel(pc, s_field2 + 3 * hb) * wb,
+                             fabsf(Fa[0]) + fabsf(Fa[1]) + fabsf(Fa[2]), e);
+                    // squares of the values scaled by 2^-100 (fields of up to ~1e35 /s stay in
+                    // range)
+                    e *= 0x1p-50f;
+                    err2 = fmaf(e, e, err2);
+                    const float u0 = v0 * 0x1p-50f, u1 = v1 * 0x1p-50f, u2 = v2 * 0x1p-50f;
+                    val2 = fmaf(u0, u0, fmaf(u1, u1, fmaf(u2, u2, val2)));
+                } else {
+                    deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, v0, v1, v2);
+                }
             };
             // the warp's grid points: prefix sum of the runs over the warp's slots, and the
             // first kJobTable of them listed as (slot, grid point) by their owners
@@ -855,6 +910,22 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             }
             __syncwarp();   // s_job / s_kp are rewritten for the next block
         }
+    }
+    if (CHECK) {   // the unit's estimated error against the values it would deposit
+        __shared__ float s_err[2];
+        if (threadIdx.x == 0) s_err[0] = s_err[1] = 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            err2 += __shfl_xor_sync(0xffffffffu, err2, o);
+            val2 += __shfl_xor_sync(0xffffffffu, val2, o);
+        }
+        __syncthreads();
+        if (lane == 0) {
+            atomicAdd(&s_err[0], err2);
+            atomicAdd(&s_err[1], val2);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_err[0] > kPrecisionTol * kPrecisionTol * s_err[1])
+            bits |= LW_ST_PRECISION;
     }
     if (timed_out) {
         bits |= LW_ST_TIMEOUT;
@@ -1111,8 +1182,18 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
 
 template <int PIX, int ACC, int FL>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
-    const int bits = mixed_cta<PIX, ACC, FL>(p, blockIdx.x, blockIdx.y);
+    const int bits = mixed_cta<PIX, ACC, FL, false>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
+}
+
+// Precision check of a mixed deposit: the units of every `stride`-th electron chunk
+// (grid y = sampled chunks), evaluated without depositing.
+template <int PIX, int FL>
+__global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
+    deposit_check_kernel(DepositArgs p, int stride) {
+    const int bits =
+        mixed_cta<PIX, kAccF32X4, FL, true>(p, blockIdx.x, (int64_t)blockIdx.y * stride);
+    block_status_or(p.status, bits & LW_ST_PRECISION);
 }
 
 // Persistent form: CTAs pull (variant, pixel tile, electron chunk) units from a
@@ -1141,9 +1222,21 @@ __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
         if (u >= n_units) break;
         const BatchUnit un = units[u];
         const DepositArgs& p = c_batch_vars[un.variant];
-        const int bits = mixed_cta<PIX, ACC, FL>(p, un.tile, un.chunk);
+        const int bits = mixed_cta<PIX, ACC, FL, false>(p, un.tile, un.chunk);
         block_status_or(p.status, bits);
     }
+}
+
+// Precision check of a batched deposit: every `stride`-th unit of the list.
+template <int PIX, int FL>
+__global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
+    deposit_batched_check_kernel(const BatchUnit* __restrict__ units, int n_units, int stride) {
+    const int u = blockIdx.x * stride;
+    if (u >= n_units) return;
+    const BatchUnit un = units[u];
+    const DepositArgs& p = c_batch_vars[un.variant];
+    const int bits = mixed_cta<PIX, kAccF32X4, FL, true>(p, un.tile, un.chunk);
+    block_status_or(p.status, bits & LW_ST_PRECISION);
 }
 
 // Zeroes every variant's record (n_pix * n_bins * words 4-byte words): grid y =
@@ -1182,6 +1275,17 @@ BatchedKernel batched_kernel_fl(uint32_t fl) {
     return fl == 1 ? deposit_batched_kernel<kMixPix, ACC, 1>
            : fl == 2 ? deposit_batched_kernel<kMixPix, ACC, 2>
                      : deposit_batched_kernel<kMixPix, ACC, 3>;
+}
+using CheckKernel = void (*)(DepositArgs, int);
+CheckKernel check_kernel(uint32_t fl) {
+    return fl == 1 ? deposit_check_kernel<kMixPix, 1>
+           : fl == 2 ? deposit_check_kernel<kMixPix, 2> : deposit_check_kernel<kMixPix, 3>;
+}
+using BatchedCheckKernel = void (*)(const BatchUnit*, int, int);
+BatchedCheckKernel batched_check_kernel(uint32_t fl) {
+    return fl == 1 ? deposit_batched_check_kernel<kMixPix, 1>
+           : fl == 2 ? deposit_batched_check_kernel<kMixPix, 2>
+                     : deposit_batched_check_kernel<kMixPix, 3>;
 }
 BatchedKernel batched_kernel(int acc, uint32_t fl) {
     return acc == kAccKahan ? batched_kernel_fl<kAccKahan>(fl)
@@ -1267,6 +1371,17 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
         cudaSuccess)
         return LW_ECUDA;
     kern<<<g, kMixThreads, smem, st>>>(a);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    if (status) {   // the precision check on a sample of the electron chunks (LW_ST_PRECISION)
+        const int64_t chunks = g.y;
+        const int stride = chunks > kCheckStride ? kCheckStride : 1;
+        const CheckKernel ck = check_kernel(field_flags);
+        if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return LW_ECUDA;
+        ck<<<dim3(g.x, (unsigned)((chunks + stride - 1) / stride)), kMixThreads, smem, st>>>(a,
+                                                                                          stride);
+    }
     return launch_status();
 }
 
@@ -1447,5 +1562,15 @@ extern "C" int lw_batch_deposit(const lw_batch* plan, void* stream) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(plan->n_units, sms * per_sm);
     kern<<<grid, kMixThreads, plan->smem_bytes, st>>>(units, plan->n_units, counter);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    // the precision check on every kCheckStride-th unit (LW_ST_PRECISION into the variants'
+    // status words)
+    const int stride = plan->n_units > kCheckStride ? kCheckStride : 1;
+    const BatchedCheckKernel ck = batched_check_kernel((uint32_t)plan->field_flags);
+    if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             plan->smem_bytes) != cudaSuccess)
+        return LW_ECUDA;
+    ck<<<(plan->n_units + stride - 1) / stride, kMixThreads, plan->smem_bytes, st>>>(
+        units, plan->n_units, stride);
     return launch_status();
 }

@@ -22,7 +22,7 @@ LW_OK, LW_EINVAL, LW_ESIZE, LW_ECUDA, LW_EUNSUPPORTED, LW_ETIMEOUT = 0, -1, -2, 
 LW_FP64, LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32, LW_MIXED_F32X4 = 0, 1, 2, 3, 4
 LW_FIELD_ACCEL, LW_FIELD_VELOCITY = 1, 2
 LW_ST_BETA, LW_ST_NONFINITE, LW_ST_TIME, LW_ST_CLIP, LW_ST_TA_ORDER, LW_ST_STEP = 1, 2, 4, 8, 16, 32
-LW_ST_TIMEOUT = 64
+LW_ST_TIMEOUT, LW_ST_PRECISION = 64, 128
 LW_SECTION_FP64, LW_SECTION_MIXED = 1, 2
 
 Q_E = 1.602176634e-19

@@ -132,7 +132,7 @@ def test_enum_values_match_the_header(tmp_path):
     import subprocess
     names = ["LW_FP64", "LW_MIXED", "LW_MIXED_KAHAN", "LW_MIXED_F32", "LW_MIXED_F32X4", "LW_FIELD_ACCEL",
              "LW_FIELD_VELOCITY", "LW_ST_BETA", "LW_ST_NONFINITE", "LW_ST_TIME", "LW_ST_CLIP",
-             "LW_ST_TA_ORDER", "LW_ST_STEP", "LW_ST_TIMEOUT", "LW_SECTION_FP64", "LW_SECTION_MIXED"]
+             "LW_ST_TA_ORDER", "LW_ST_STEP", "LW_ST_TIMEOUT", "LW_ST_PRECISION", "LW_SECTION_FP64", "LW_SECTION_MIXED"]
     src = tmp_path / "enums.c"
     src.write_text("#include <stdio.h>\n#include \"lw.h\"\nint main(void) {\n" +
                    "".join(f'  printf("%d\\n", (int){n});\n' for n in names) +

@@ -85,3 +85,25 @@ def test_grid_points_reached_counts_the_exact_end_bins():
             u1 = (ta1[m, k] - t_min) / dt_u
             want += sum(1 for j in range(n_bins) if math.floor(u0) < j <= math.floor(u1))
     assert got == want
+
+
+def test_deposit_roofline_picks_the_binding_pipe():
+    """The work model and the bound with the largest fraction of its measured peak."""
+    b = _bench()
+    from paper_2206_03015_gb300 import lw
+    w = b.deposit_work(10_000, 10_000, 4096, 65_536, 512, 885_159_358, lw.LW_MIXED_F32X4)
+    assert w["pixel_blocks"] == 4096 * 10_000 * 20     # 10,000 steps in blocks of 512
+    assert w["l2_ops"] == 885_159_358
+    assert w["hbm_bytes"] == 10_000 * (10_001 * 40 + 20 * 32) + 4096 * 3 * 65_536 * 4
+    assert w["fp32_flops"] == 885_159_358 * 86 + 4096 * 10_000 * 20 * 47
+    w3 = b.deposit_work(10_000, 10_000, 4096, 65_536, 512, 100, lw.LW_MIXED)
+    assert w3["l2_ops"] == 300 and w3["hbm_bytes"] > w["hbm_bytes"]
+    peaks = {"red_v4f32_lines": {"ops_per_s": 2.0e11}, "fma_f32": {"flops": 75e12},
+             "lds_v4": {"bytes_per_s": 40e12}}
+    r = b.deposit_roofline(w, 10.0, peaks, 6800.0)
+    t = 10e-3
+    assert r["bound"] == "l2_red"
+    assert math.isclose(r["achieved"], 885_159_358 / t / 1e9)
+    assert math.isclose(r["frac"], 885_159_358 / t / 2.0e11)
+    for k, v in r["bounds"].items():
+        assert v["frac"] <= r["frac"] and math.isclose(v["frac"], v["achieved"] / v["peak"])

@@ -272,3 +272,45 @@ def test_config3_mixed_spectrum_per_band():
         assert band.sum() > w.n_pix
         err = np.linalg.norm((S - S_o)[band]) / np.linalg.norm(S_o[band])
         assert err <= tol, (h, err)
+
+
+def test_precision_bit_flags_a_coarsely_sampled_synchrotron_flash():
+    """LW_ST_PRECISION: an observer in the orbit plane of electrons circling at beta = 0.999,
+    sampled 100 times per turn, sees a flash that changes by a large fraction across a
+    step; the mixed deposit's FP32 weights and Doppler factors err by more than 1e-4 of
+    the spectrum (checked against the oracle) and every mixed record reports it.  The FP64
+    path matches the oracle and reports nothing."""
+    dt = 1e-16
+    tr = simple.circular_motion(4096, dt, 0.999, 2 * math.pi / (100 * dt), n_e=4)
+    ang = np.linspace(-0.02, 0.02, 4)
+    n_hat = np.stack([np.cos(ang), np.zeros_like(ang), np.sin(ang)], -1)
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+    grid = lw.grid_from_bounds(lo, hi, 8192)
+    o = oracle_run(tr, n_hat, grid)
+    g64 = gpu_run(tr, n_hat, grid, lw.LW_FP64, block=512)
+    assert g64["status"] & lw.LW_ST_PRECISION == 0
+    assert rel_l2(g64["S"], o["S"]) <= FP64_TOL
+    for prec in (lw.LW_MIXED, lw.LW_MIXED_KAHAN, lw.LW_MIXED_F32, lw.LW_MIXED_F32X4):
+        g = gpu_run(tr, n_hat, grid, prec, block=512)
+        assert rel_l2(g["S"], o["S"]) > MIXED_TOL
+        assert g["status"] & lw.LW_ST_PRECISION, prec
+
+
+def test_precision_bit_quiet_on_a_resolved_bunch():
+    """No LW_ST_PRECISION on a Boris-pushed bunch in the laser (300 electrons, 3,000 steps,
+    32 x 32 pixels, 65,536 bins), whose mixed spectrum is within 1e-4 of the FP64 one."""
+    w = configs.c2_paper(n_e=300, n_s=3000, nx=32)
+    tr = w.traj
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot)
+    det = lw.Detector(w.n_hat)
+    b = lw.lw_grid_bounds(traj, det).cpu().numpy()
+    grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
+    S64 = lw.lw_spectrum(lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64), lw.LW_FP64,
+                         det.n_pix, grid)
+    for prec in (lw.LW_MIXED, lw.LW_MIXED_F32X4):
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        S = lw.lw_spectrum(lw.lw_deposit_time_domain(traj, det, grid, prec, status=st), prec,
+                           det.n_pix, grid)
+        torch.cuda.synchronize()
+        assert int(st.item()) & lw.LW_ST_PRECISION == 0
+        assert float(torch.linalg.norm(S.double() - S64) / torch.linalg.norm(S64)) <= MIXED_TOL

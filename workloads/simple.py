@@ -133,3 +133,25 @@ def random_smooth(n_e: int, n_s: int, dt: float, seed: int, gamma: float = 20.0,
     bd = np.stack([bperp_dot[:, 0], bperp_dot[:, 1], bz_dot], axis=-1)
     return Trajectories(np.ascontiguousarray(t), np.ascontiguousarray(r),
                         np.ascontiguousarray(beta), np.ascontiguousarray(bd))
+
+
+def transverse_oscillation(n_e: int, n_s: int, dt: float, beta_z: float, amp: float,
+                           samples_per_period: float, seed: int = 0) -> Trajectories:
+    """Electrons drifting along z at beta_z with a transverse velocity oscillation
+    beta_x = amp sin(omega t + phase_k), sampled samples_per_period times per period
+    (positions integrated analytically, beta_dot = d beta / dt).  Few samples per period
+    make the field change by a large fraction across each step."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = dt * np.arange(n_s + 1, dtype=np.float64)
+    omega = 2.0 * np.pi / (samples_per_period * dt)
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=(n_e, 1))
+    z0 = rng.normal(scale=1e-9, size=(n_e, 1))
+    r = np.zeros((n_e, n_s + 1, 3))
+    beta = np.zeros_like(r)
+    bd = np.zeros_like(r)
+    r[..., 0] = -amp * C0 / omega * np.cos(omega * t + ph)
+    r[..., 2] = z0 + beta_z * C0 * t
+    beta[..., 0] = amp * np.sin(omega * t + ph)
+    beta[..., 2] = beta_z
+    bd[..., 0] = amp * omega * np.cos(omega * t + ph)
+    return Trajectories(t, r, beta, bd)
