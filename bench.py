@@ -667,6 +667,126 @@ def run_c5(args):
             "sequential": {"value": dep / (ms_seq * 1e-3), "ms_per_step": ms_seq}}
 
 
+# ----------------------------------------------------------------------------- C4 gradient
+
+def run_c4(args):
+    """Config 4: gradient of the band-integrated spectral energy (+-5 % of the on-axis
+    fundamental) with respect to every electron's initial momentum and the laser's a0 and
+    w0, through the library's kernels only (GPU Boris push, FP64 deposit and spectrum,
+    lw_spectrum_grad, forward-mode lw_boris_push_grad); each part timed with CUDA events.
+    Beside it, once, the same gradient with the torch-written checkpointed pusher."""
+    import torch
+
+    from paper_2206_03015_gb300 import lw
+    from paper_2206_03015_gb300.autograd import (LWSpectrum, PushSpectrum, band_energy,
+                                                 band_mask, boris_push)
+    from workloads import configs
+    from workloads.planewave import doppler_fundamental
+
+    dev = torch.device("cuda", 0)
+    r0n, u0n, laser, t0, t1, n_s, n_hat, n_bins, gamma = configs.c4_setup(
+        n_e=args.c4_ne, n_s=args.c4_ns, nx=args.c4_nx, n_bins=args.c4_bins)
+    n_e = r0n.shape[0]
+    det = lw.Detector(n_hat, device=dev)
+    r0 = torch.from_numpy(r0n).to(dev)
+    L4 = (laser.lam, laser.a0, laser.w0, laser.fwhm)
+    dt = (t1 - t0) / n_s
+    # the grid from one forward push (Eqs. tu_min / tu_max)
+    t = torch.empty(n_s + 1, dtype=torch.float64, device=dev)
+    R, B, A = (torch.empty((n_e, n_s + 1, 3), dtype=torch.float64, device=dev) for _ in range(3))
+    lw.lw_boris_push(r0.clone(), torch.from_numpy(u0n).to(dev), t0, dt, n_s, L4, t, R, B, A)
+    traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_FP64, device=dev)
+    bnd = lw.lw_grid_bounds(traj, det).cpu().numpy()
+    grid = lw.grid_from_bounds(bnd[0], bnd[1], n_bins)
+    mask = band_mask(grid, doppler_fundamental(gamma, laser.lam, laser.a0), 0.05)
+    del traj, t, R, B, A
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def grad_step():
+        u = torch.from_numpy(u0n).to(dev).requires_grad_(True)
+        a0 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
+        w0 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
+        e0 = ev()
+        S = PushSpectrum.apply(u, a0, w0, r0, laser.lam, laser.fwhm, t0, t1, n_s, det, grid)
+        L = band_energy(S, grid, mask)
+        e1 = ev()
+        L.backward()
+        e2 = ev()
+        return L, u.grad, a0.grad, w0.grad, (e0, e1, e2)
+
+    for _ in range(args.warmup):
+        grad_step()
+    torch.cuda.synchronize()
+    fw, bw = [], []
+    s0 = ev()
+    for _ in range(args.steps):
+        L, gu, ga, gw, (e0, e1, e2) = grad_step()
+    s1 = ev()
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / args.steps
+    # the parts, once more, each bracketed by events
+    parts = {}
+    u0d = torch.from_numpy(u0n).to(dev)
+    t = torch.empty(n_s + 1, dtype=torch.float64, device=dev)
+    R, B, A = (torch.empty((n_e, n_s + 1, 3), dtype=torch.float64, device=dev) for _ in range(3))
+    marks = [ev()]
+    lw.lw_boris_push(r0.clone(), u0d.clone(), t0, dt, n_s, L4, t, R, B, A)
+    marks.append(ev())
+    traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_FP64, device=dev)
+    marks.append(ev())
+    rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
+    marks.append(ev())
+    S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, want_X=True)
+    marks.append(ev())
+    gS = (mask.to(dev) * (2.0 * math.pi / (grid.n_bins * grid.dt_u)))[None, :].expand_as(S)
+    g_r, g_b, g_a = lw.lw_spectrum_grad(traj, det, grid, X, gS.contiguous())
+    marks.append(ev())
+    lw.lw_boris_push_grad(r0, u0d, t0, dt, n_s, L4, g_r, g_b, g_a)
+    marks.append(ev())
+    torch.cuda.synchronize()
+    for name, a, b in zip(("push", "upload", "deposit_fp64", "spectrum_fp64", "spectrum_grad",
+                           "push_grad"), marks[:-1], marks[1:]):
+        parts[name] = a.elapsed_time(b)
+    del traj, rec, S, X, g_r, g_b, g_a, t, R, B, A
+    # the torch-written checkpointed pusher (autograd) with the library's deposit adjoint
+    ref = None
+    if not args.no_torch_pusher:
+        u = torch.from_numpy(u0n).to(dev).requires_grad_(True)
+        a0 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
+        w0 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
+        torch.cuda.synchronize()
+        e0 = ev()
+        tt, rr, bb, aa = boris_push(r0, u, a0, w0, laser.lam, laser.fwhm, t0, t1, n_s,
+                                    checkpoint_every=256)
+        L2 = band_energy(LWSpectrum.apply(tt, rr, bb, aa, det, grid), grid, mask)
+        L2.backward()
+        e1 = ev()
+        torch.cuda.synchronize()
+        ref = {"ms": e0.elapsed_time(e1),
+               "grad_rel_diff_u0": float(torch.linalg.norm(u.grad - gu) / torch.linalg.norm(gu)),
+               "grad_rel_diff_a0": float(abs(a0.grad - ga) / abs(ga)),
+               "grad_rel_diff_w0": float(abs(w0.grad - gw) / abs(gw))}
+    dep = n_e * n_s * det.n_pix
+    return {"metric": METRIC, "value": dep / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"c4 gradient: {n_e} co-located electrons (gamma 60 +-0.1%) x "
+                                   f"{n_s} Boris steps in a 1 um, a0 = 1, 10 fs, w0 = 20 um laser, "
+                                   f"{int(round(det.n_pix ** 0.5))}^2 pixels over +-1/gamma, "
+                                   f"{n_bins} bins; loss = spectral energy within +-5% of the "
+                                   f"on-axis fundamental; gradient w.r.t. u0 (all electrons), a0, w0",
+                       "deposits_per_step": dep,
+                       "step": "forward (push, upload, FP64 deposit, spectrum) + backward "
+                               "(lw_spectrum_grad, lw_boris_push_grad)"},
+            "parts_ms": parts, "loss": float(L), "grad_a0": float(ga), "grad_w0": float(gw),
+            "torch_pusher": ref}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -737,7 +857,12 @@ def main():
     ap.add_argument("--shard", default="pixels", choices=["pixels", "detectors"],
                     help="N > 1: split one detector's pixels (strong scaling) or give each "
                          "rank a detector of its own (weak scaling)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
+    ap.add_argument("--c4-ne", type=int, default=2048)
+    ap.add_argument("--c4-ns", type=int, default=4096)
+    ap.add_argument("--c4-nx", type=int, default=32)
+    ap.add_argument("--c4-bins", type=int, default=16_384)
+    ap.add_argument("--no-torch-pusher", action="store_true")
     ap.add_argument("--c5-variants", type=int, default=64)
     ap.add_argument("--c5-ne", type=int, nargs=2, default=(128, 1024))
     ap.add_argument("--c5-ns", type=int, nargs=2, default=(2000, 8000))
@@ -759,6 +884,8 @@ def main():
         res = run_reference(args, rank, world)
     elif args.workload == "c5":
         res = run_c5(args)
+    elif args.workload == "c4":
+        res = run_c4(args)
     else:
         res = run_ours(args, rank, world, dist)
     if rank == 0 and res is not None:

@@ -319,6 +319,25 @@ int lw_boris_push(double* r, double* u, int64_t n_e, double t0, double dt, int64
                   double* t_out, double* r_out, double* beta_out, double* bdot_out,
                   void* stream);
 
+/* Gradient through lw_boris_push (one call from step 0): given dL/d(sample) for every
+ * sample of the trajectories that lw_boris_push(r0, u0, n_e, t0, dt, 0, n_steps, laser,
+ * charge, mass, ...) writes -- dL_dr, dL_dbeta, dL_dbeta_dot [n_e][n_steps+1][3] (device,
+ * float64; e.g. from lw_spectrum_grad) -- adds
+ *   dL_du0     [n_e][3]  the gradient with respect to each electron's initial u = gamma beta
+ *   dL_dlaser  [2]       the gradient with respect to the laser's a0 and w0 (summed over
+ *                        the electrons with FP64 atomics)
+ * (device, float64, caller-zeroed or accumulated).  Each electron is pushed again with
+ * forward-mode derivatives of its state along u0_x, u0_y, u0_z, a0 and w0, the same
+ * operations as lw_boris_push, and each sample's derivatives are contracted with its
+ * dL/d(sample) (the chain rule through Eqs. far_adv / far_efield is in lw_spectrum_grad;
+ * this is the "update trajectory" step of Algorithm 2 differentiated).  No trajectory
+ * state is stored: memory is the inputs' and outputs'.
+ * Errors: LW_EINVAL, LW_ECUDA. */
+int lw_boris_push_grad(const double* r0, const double* u0, int64_t n_e, double t0, double dt,
+                       int32_t n_steps, const lw_laser* laser, double charge, double mass,
+                       const double* dL_dr, const double* dL_dbeta, const double* dL_dbeta_dot,
+                       double* dL_du0, double* dL_dlaser, void* stream);
+
 /* Several independent problems ("variants": own trajectories, detector, grid
  * and record) deposited by one persistent launch of the mixed-precision
  * deposit (LW_MIXED, LW_MIXED_KAHAN, LW_MIXED_F32 or LW_MIXED_F32X4).  The work is

@@ -1,13 +1,19 @@
 """Differentiable spectra: gradients of a band-integrated spectral yield with
 respect to per-electron initial momenta and the laser's a0 and waist.
 
+``PushSpectrum`` is the whole chain in the library's kernels: the GPU Boris push
+(lw_boris_push), the FP64 deposit and spectrum, and in reverse lw_spectrum_grad
+followed by lw_boris_push_grad (the push differentiated in forward mode along
+u0, a0 and w0, so no trajectory state is stored or recomputed).
+
 ``LWSpectrum`` wraps the library's FP64 forward (upload, deposit, spectrum)
 and its adjoint (lw_spectrum_grad) as a torch.autograd.Function of the
 trajectory samples (r, beta, beta_dot).  ``boris_push`` produces those samples
 from initial conditions and laser parameters with the Boris method written in
 torch, so autograd carries the gradient on to (u0, a0, w0); the pusher is
 split into segments of ``checkpoint_every`` steps that are recomputed during
-the backward pass, so the autograd graph holds one segment at a time.
+the backward pass, so the autograd graph holds one segment at a time.  It is
+the independent formulation the kernel chain is tested against.
 """
 from __future__ import annotations
 
@@ -43,6 +49,44 @@ class LWSpectrum(torch.autograd.Function):
         g_r, g_b, g_a = lw.lw_spectrum_grad(ctx.traj, ctx.det, ctx.grid, X, gS.contiguous(),
                                             q=ctx.q)
         return None, g_r, g_b, g_a, None, None, None
+
+
+class PushSpectrum(torch.autograd.Function):
+    """S[m][l] (FP64) of electrons pushed by the library's Boris kernel (lw_boris_push) from
+    (r0, u0) through the Gaussian laser (lam, a0, w0, fwhm), as a function of u0 [n_e, 3] and
+    the 0-d tensors a0 and w0.  Backward: lw_spectrum_grad (deposit and FFT transposed) then
+    lw_boris_push_grad (the push differentiated in forward mode along u0, a0 and w0) -- every
+    step in the library's kernels."""
+
+    @staticmethod
+    def forward(ctx, u0, a0, w0, r0, lam: float, fwhm: float, t_start: float, t_end: float,
+                n_steps: int, det: "lw.Detector", grid: "lw.Grid", q: float = Q_E):
+        dev = u0.device
+        n_e = u0.shape[0]
+        dt = (t_end - t_start) / n_steps
+        laser = (lam, float(a0), float(w0), fwhm)
+        t = torch.empty(n_steps + 1, dtype=torch.float64, device=dev)
+        R, B, A = (torch.empty((n_e, n_steps + 1, 3), dtype=torch.float64, device=dev)
+                   for _ in range(3))
+        r0 = r0.detach().to(torch.float64).contiguous()
+        u0d = u0.detach().to(torch.float64).contiguous()
+        lw.lw_boris_push(r0.clone(), u0d.clone(), t_start, dt, n_steps, laser, t, R, B, A)
+        traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_FP64, device=dev)
+        rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
+        S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, q=q, want_X=True)
+        ctx.traj, ctx.det, ctx.grid, ctx.q = traj, det, grid, q
+        ctx.push = (t_start, dt, n_steps, laser)
+        ctx.save_for_backward(X, r0, u0d)
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        X, r0, u0 = ctx.saved_tensors
+        g_r, g_b, g_a = lw.lw_spectrum_grad(ctx.traj, ctx.det, ctx.grid, X, gS.contiguous(),
+                                            q=ctx.q)
+        t_start, dt, n_steps, laser = ctx.push
+        du0, dlaser = lw.lw_boris_push_grad(r0, u0, t_start, dt, n_steps, laser, g_r, g_b, g_a)
+        return (du0, dlaser[0], dlaser[1], None, None, None, None, None, None, None, None, None)
 
 
 def band_mask(grid: "lw.Grid", omega_center: float, rel_half_width: float = 0.05):

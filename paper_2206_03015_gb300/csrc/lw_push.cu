@@ -1,7 +1,9 @@
 // Boris pusher on the GPU (FP64), the trajectory update of Algorithm 2 ("update
 // trajectory" in the step loop), for the in-situ form of the time-domain path:
 // trajectories are produced one block of steps at a time and deposited at once,
-// so only the current block is ever stored.
+// so only the current block is ever stored.  The same step, carried out on
+// forward-mode derivative numbers, gives the gradient of a loss of the samples
+// with respect to the initial momenta and the laser's a0 and waist.
 //
 // Laser: lowest-order paraxial Gaussian beam polarised along x, propagating
 // along -z, focused at z = 0 and peaking there at t = 0:
@@ -23,42 +25,204 @@ namespace {
 constexpr double kQe = 1.602176634e-19;
 constexpr double kMe = 9.1093837015e-31;
 
-struct Laser {
-    double omega, k, sigma, E0, zR, w0;
-};
+using ::atan;
+using ::cos;
+using ::exp;
+using ::sqrt;
 
-__device__ __forceinline__ void fields(const Laser& L, double x, double y, double z, double t,
-                                       double& Ex, double& By) {
-    const double zeta = -z;
-    const double w = L.w0 * sqrt(1.0 + (zeta / L.zR) * (zeta / L.zR));
-    const double rho2 = x * x + y * y;
-    const double xi = t + z * kInvC0;
-    const double env = exp(-rho2 / (w * w)) * exp(-(xi * xi) / (2.0 * L.sigma * L.sigma));
-    const double phase =
+// Forward-mode derivative numbers: a value and its derivatives along N directions.
+template <int N>
+struct Dual {
+    double v;
+    double d[N];
+};
+template <int N>
+__device__ __forceinline__ Dual<N> mk(double v) {
+    Dual<N> r;
+    r.v = v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = 0.0;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
+    Dual<N> r;
+    r.v = -a.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r;
+    r.v = a.v / b.v;
+    const double ib = 1.0 / b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, double b) {
+    Dual<N> r = a;
+    r.v = a.v + b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(double a, const Dual<N>& b) { return b + a; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, double b) { return a + (-b); }
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(double a, const Dual<N>& b) { return (-b) + a; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, double b) {
+    Dual<N> r;
+    r.v = a.v * b;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(double a, const Dual<N>& b) { return b * a; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, double b) { return a * (1.0 / b); }
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(double a, const Dual<N>& b) { return mk<N>(a) / b; }
+template <int N>
+__device__ __forceinline__ Dual<N> sqrt(const Dual<N>& a) {
+    Dual<N> r;
+    r.v = sqrt(a.v);
+    const double h = 0.5 / r.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> exp(const Dual<N>& a) {
+    Dual<N> r;
+    r.v = exp(a.v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * r.v;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> cos(const Dual<N>& a) {
+    Dual<N> r;
+    double sn, cs;
+    sincos(a.v, &sn, &cs);
+    r.v = cs;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = -a.d[i] * sn;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> atan(const Dual<N>& a) {
+    Dual<N> r;
+    r.v = atan(a.v);
+    const double h = 1.0 / (1.0 + a.v * a.v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
+    return r;
+}
+
+// Laser constants (T = double, or Dual when derivatives along a0 and w0 are carried).
+template <typename T>
+struct LaserT {
+    double omega, k, sigma;
+    T E0, zR, w0;
+};
+using Laser = LaserT<double>;
+
+template <typename T>
+__device__ __forceinline__ void fields(const LaserT<T>& L, const T& x, const T& y, const T& z,
+                                       double t, T& Ex, T& By) {
+    const T zeta = -z;
+    const T w = L.w0 * sqrt(1.0 + (zeta / L.zR) * (zeta / L.zR));
+    const T rho2 = x * x + y * y;
+    const T xi = t + z * kInvC0;
+    const T env = exp(-rho2 / (w * w)) * exp(-(xi * xi) / (2.0 * L.sigma * L.sigma));
+    const T phase =
         L.omega * xi + L.k * rho2 * zeta / (2.0 * (zeta * zeta + L.zR * L.zR)) - atan(zeta / L.zR);
     Ex = L.E0 * (L.w0 / w) * env * cos(phase);
     By = -Ex * kInvC0;
 }
 
+// The sample at (r, u): beta = u / gamma and the Lorentz-force beta_dot.
+template <typename T>
+__device__ __forceinline__ void sample(const LaserT<T>& L, double qm, const T r[3], const T u[3],
+                                       double t, T b[3], T a[3]) {
+    const T gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    b[0] = u[0] / gam;
+    b[1] = u[1] / gam;
+    b[2] = u[2] / gam;
+    T Ex, By;
+    fields(L, r[0], r[1], r[2], t, Ex, By);
+    // E = (Ex, 0, 0), B = (0, By, 0): beta x B = (-b_z By, 0, b_x By)
+    const T bE = b[0] * Ex;
+    const T f = qm / (gam * kC0);
+    a[0] = f * (Ex + kC0 * (-b[2] * By) - b[0] * bE);
+    a[1] = f * (-b[1] * bE);
+    a[2] = f * (kC0 * (b[0] * By) - b[2] * bE);
+}
+
+// One Boris step from time ti: drift dt/2, kick with the fields at the midpoint, drift.
+template <typename T>
+__device__ __forceinline__ void boris_step(const LaserT<T>& L, double qm, double dt, double ti,
+                                           T x[3], T v[3]) {
+    const double eps = qm * dt / (2.0 * kC0);
+    T gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const T rh[3] = {x[0] + 0.5 * dt * kC0 * v[0] / gam, x[1] + 0.5 * dt * kC0 * v[1] / gam,
+                     x[2] + 0.5 * dt * kC0 * v[2] / gam};
+    T Ex, By;
+    fields(L, rh[0], rh[1], rh[2], ti + 0.5 * dt, Ex, By);
+    const T um[3] = {v[0] + eps * Ex, v[1], v[2]};
+    const T gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const T tv = qm * dt / (2.0 * gm) * By;   // t vector = (0, tv, 0)
+    // u' = um + um x t ; s = 2 t / (1 + t^2) ; u+ = um + u' x s
+    const T up[3] = {um[0] - um[2] * tv, um[1], um[2] + um[0] * tv};
+    const T sv = 2.0 * tv / (1.0 + tv * tv);
+    v[0] = um[0] - up[2] * sv + eps * Ex;
+    v[1] = um[1];
+    v[2] = um[2] + up[0] * sv;
+    gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    x[0] = rh[0] + 0.5 * dt * kC0 * v[0] / gam;
+    x[1] = rh[1] + 0.5 * dt * kC0 * v[1] / gam;
+    x[2] = rh[2] + 0.5 * dt * kC0 * v[2] / gam;
+}
+
 __device__ __forceinline__ void store_sample(const Laser& L, double qm, const double r[3],
                                              const double u[3], double t, double* ro,
                                              double* bo, double* ao) {
-    const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const double b[3] = {u[0] / gam, u[1] / gam, u[2] / gam};
-    double Ex, By;
-    fields(L, r[0], r[1], r[2], t, Ex, By);
-    // E = (Ex, 0, 0), B = (0, By, 0): beta x B = (-b_z By, 0, b_x By)
-    const double bE = b[0] * Ex;
-    const double f = qm / (gam * kC0);
-    ro[0] = r[0];
-    ro[1] = r[1];
-    ro[2] = r[2];
-    bo[0] = b[0];
-    bo[1] = b[1];
-    bo[2] = b[2];
-    ao[0] = f * (Ex + kC0 * (-b[2] * By) - b[0] * bE);
-    ao[1] = f * (-b[1] * bE);
-    ao[2] = f * (kC0 * (b[0] * By) - b[2] * bE);
+    double b[3], a[3];
+    sample(L, qm, r, u, t, b, a);
+    for (int c = 0; c < 3; ++c) {
+        ro[c] = r[c];
+        bo[c] = b[c];
+        ao[c] = a[c];
+    }
 }
 
 __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int64_t n_e,
@@ -72,28 +236,8 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
         const int64_t base = k * (int64_t)(n_steps + 1);
         store_sample(L, qm, x, v, t0 + dt * (double)step0, ro + 3 * base, bo + 3 * base,
                      ao + 3 * base);
-        const double eps = qm * dt / (2.0 * kC0);
         for (int s = 0; s < n_steps; ++s) {
-            const double ti = t0 + dt * (double)(step0 + s);
-            double gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            const double rh[3] = {x[0] + 0.5 * dt * kC0 * v[0] / gam,
-                                  x[1] + 0.5 * dt * kC0 * v[1] / gam,
-                                  x[2] + 0.5 * dt * kC0 * v[2] / gam};
-            double Ex, By;
-            fields(L, rh[0], rh[1], rh[2], ti + 0.5 * dt, Ex, By);
-            const double um[3] = {v[0] + eps * Ex, v[1], v[2]};
-            const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-            const double tv = qm * dt / (2.0 * gm) * By;   // t vector = (0, tv, 0)
-            // u' = um + um x t ; s = 2 t / (1 + t^2) ; u+ = um + u' x s
-            const double up[3] = {um[0] - um[2] * tv, um[1], um[2] + um[0] * tv};
-            const double sv = 2.0 * tv / (1.0 + tv * tv);
-            v[0] = um[0] - up[2] * sv + eps * Ex;
-            v[1] = um[1];
-            v[2] = um[2] + up[0] * sv;
-            gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            x[0] = rh[0] + 0.5 * dt * kC0 * v[0] / gam;
-            x[1] = rh[1] + 0.5 * dt * kC0 * v[1] / gam;
-            x[2] = rh[2] + 0.5 * dt * kC0 * v[2] / gam;
+            boris_step(L, qm, dt, t0 + dt * (double)(step0 + s), x, v);
             const int64_t o = 3 * (base + s + 1);
             store_sample(L, qm, x, v, t0 + dt * (double)(step0 + s + 1), ro + o, bo + o, ao + o);
         }
@@ -103,6 +247,52 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
         u[3 * k] = v[0];
         u[3 * k + 1] = v[1];
         u[3 * k + 2] = v[2];
+    }
+}
+
+// Gradient of a loss L(samples) with respect to each electron's initial momentum u0 and
+// the laser's a0 and w0, by forward-mode differentiation of the push: every electron is
+// pushed again carrying the derivatives of its state along u0_x, u0_y, u0_z, a0 and w0
+// (Dual<5>), and each sample's derivatives are contracted with dL/d(r, beta, beta_dot)
+// of that sample.  Per-electron a0 and w0 parts are added to dL_dlaser with FP64 atomics.
+constexpr int kTan = 5;
+__global__ void push_tangent_kernel(const double* __restrict__ r0, const double* __restrict__ u0,
+                                    int64_t n_e, double t0, double dt, int n_steps,
+                                    LaserT<Dual<kTan>> L, double qm,
+                                    const double* __restrict__ g_r, const double* __restrict__ g_b,
+                                    const double* __restrict__ g_a, double* __restrict__ dL_du0,
+                                    double* __restrict__ dL_dlaser) {
+    using D = Dual<kTan>;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        D x[3], v[3];
+        for (int c = 0; c < 3; ++c) {
+            x[c] = mk<kTan>(r0[3 * k + c]);
+            v[c] = mk<kTan>(u0[3 * k + c]);
+            v[c].d[c] = 1.0;   // directions 0..2: u0
+        }
+        double acc[kTan];
+#pragma unroll
+        for (int i = 0; i < kTan; ++i) acc[i] = 0.0;
+        const int64_t base = k * (int64_t)(n_steps + 1);
+        auto contract = [&](int64_t o, double t) {
+            D b[3], a[3];
+            sample(L, qm, x, v, t, b, a);
+            for (int c = 0; c < 3; ++c) {
+                const double gr = g_r[3 * o + c], gb = g_b[3 * o + c], ga = g_a[3 * o + c];
+#pragma unroll
+                for (int i = 0; i < kTan; ++i)
+                    acc[i] = fma(gr, x[c].d[i], fma(gb, b[c].d[i], fma(ga, a[c].d[i], acc[i])));
+            }
+        };
+        contract(base, t0);
+        for (int s = 0; s < n_steps; ++s) {
+            boris_step(L, qm, dt, t0 + dt * (double)s, x, v);
+            contract(base + s + 1, t0 + dt * (double)(s + 1));
+        }
+        for (int c = 0; c < 3; ++c) dL_du0[3 * k + c] += acc[c];
+        atomicAdd(dL_dlaser, acc[3]);
+        atomicAdd(dL_dlaser + 1, acc[4]);
     }
 }
 
@@ -140,5 +330,32 @@ extern "C" int lw_boris_push(double* r, double* u, int64_t n_e, double t0, doubl
     const int blocks = (int)((n_e + threads - 1) / threads);
     push_kernel<<<blocks, threads, 0, st>>>(r, u, n_e, t0, dt, step0, n_steps, L, charge / mass, r_out,
                                             beta_out, bdot_out);
+    return launch_status();
+}
+
+extern "C" int lw_boris_push_grad(const double* r0, const double* u0, int64_t n_e, double t0,
+                                  double dt, int32_t n_steps, const lw_laser* laser,
+                                  double charge, double mass, const double* dL_dr,
+                                  const double* dL_dbeta, const double* dL_dbeta_dot,
+                                  double* dL_du0, double* dL_dlaser, void* stream) {
+    if (!r0 || !u0 || !laser || !dL_dr || !dL_dbeta || !dL_dbeta_dot || !dL_du0 || !dL_dlaser)
+        return LW_EINVAL;
+    if (n_e < 1 || n_steps < 1 || !(dt > 0.0) || !isfinite(t0) || !(mass > 0.0))
+        return LW_EINVAL;
+    if (!(laser->lam > 0.0) || !(laser->w0 > 0.0) || !(laser->fwhm > 0.0)) return LW_EINVAL;
+    LaserT<Dual<kTan>> L;
+    L.omega = 2.0 * kPi * kC0 / laser->lam;
+    L.k = L.omega * kInvC0;
+    L.sigma = laser->fwhm / (2.0 * sqrt(log(2.0)));
+    const double e0_per_a0 = kMe * kC0 * L.omega / kQe;
+    L.E0 = Dual<kTan>{laser->a0 * e0_per_a0, {0.0, 0.0, 0.0, e0_per_a0, 0.0}};   // direction 3: a0
+    L.zR = Dual<kTan>{kPi * laser->w0 * laser->w0 / laser->lam,
+                      {0.0, 0.0, 0.0, 0.0, 2.0 * kPi * laser->w0 / laser->lam}};  // direction 4: w0
+    L.w0 = Dual<kTan>{laser->w0, {0.0, 0.0, 0.0, 0.0, 1.0}};
+    const int threads = 64;
+    const int blocks = (int)((n_e + threads - 1) / threads);
+    push_tangent_kernel<<<blocks, threads, 0, as_stream(stream)>>>(
+        r0, u0, n_e, t0, dt, n_steps, L, charge / mass, dL_dr, dL_dbeta, dL_dbeta_dot, dL_du0,
+        dL_dlaser);
     return launch_status();
 }

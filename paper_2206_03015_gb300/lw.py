@@ -87,7 +87,7 @@ _lib = None
 
 EXPORTS = ("lw_trajectories_upload", "lw_grid_bounds", "lw_deposit_time_domain", "lw_spectrum",
            "lw_spectrum_grad", "lw_spectrum_static", "lw_batch_plan", "lw_batch_deposit",
-           "lw_spectrum_fdm", "lw_boris_push")
+           "lw_spectrum_fdm", "lw_boris_push", "lw_boris_push_grad")
 
 
 def library_path() -> str:
@@ -123,6 +123,10 @@ def load(build_if_missing: bool = True):
         lib.lw_boris_push.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(lw_laser),
                                       ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+        lib.lw_boris_push_grad.argtypes = [P, P, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int32,
+                                           ctypes.POINTER(lw_laser), ctypes.c_double,
+                                           ctypes.c_double, P, P, P, P, P, P]
         lib.lw_spectrum_fdm.argtypes = [ctypes.POINTER(lw_traj), ctypes.POINTER(lw_detector),
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         ctypes.c_double, ctypes.c_double, P, P]
@@ -468,6 +472,26 @@ def lw_boris_push(r, u, t0: float, dt: float, n_steps: int, laser, t_out, r_out,
                                               float(charge), float(mass), _ptr(t_out),
                                               _ptr(r_out), _ptr(beta_out), _ptr(bdot_out),
                                               _stream()))
+
+
+def lw_boris_push_grad(r0, u0, t0: float, dt: float, n_steps: int, laser, dL_dr, dL_dbeta,
+                       dL_dbeta_dot, charge: float = -Q_E, mass: float = M_E, out=None):
+    """Gradient through lw_boris_push from (r0, u0) (float64 CUDA tensors [n_e, 3], read
+    only) over n_steps steps: given dL/d(r, beta, beta_dot) [n_e, n_steps+1, 3], returns
+    (dL/du0 [n_e, 3], dL/d(a0, w0) [2]) (added to ``out`` when given)."""
+    lib = load()
+    dev = u0.device
+    if out is None:
+        out = (torch.zeros_like(u0, dtype=torch.float64),
+               torch.zeros(2, dtype=torch.float64, device=dev))
+    L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
+    gr, gb, ga = (x.contiguous() for x in (dL_dr, dL_dbeta, dL_dbeta_dot))
+    _check("lw_boris_push_grad",
+           lib.lw_boris_push_grad(_ptr(r0.contiguous()), _ptr(u0.contiguous()), u0.shape[0],
+                                  float(t0), float(dt), int(n_steps), ctypes.byref(L),
+                                  float(charge), float(mass), _ptr(gr), _ptr(gb), _ptr(ga),
+                                  _ptr(out[0]), _ptr(out[1]), _stream()))
+    return out
 
 
 def lw_spectrum_static(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E,

@@ -19,7 +19,8 @@ import torch
 
 import oracle
 from paper_2206_03015_gb300 import lw
-from paper_2206_03015_gb300.autograd import LWSpectrum, band_energy, band_mask, boris_push
+from paper_2206_03015_gb300.autograd import (LWSpectrum, PushSpectrum, band_energy, band_mask,
+                                             boris_push)
 from workloads import simple
 from workloads.boris import GaussianLaser, boris_trajectories
 from workloads.planewave import doppler_fundamental
@@ -142,11 +143,24 @@ def test_band_energy_gradient_wrt_initial_conditions_and_laser():
             return v, laser.a0, laser.w0
         return f
 
-    checks = [(f"u0[{k},{c}]", float(u.grad[k, c]), kink_free_fd(shift_u(k, c), gamma))
-              for (k, c) in ((0, 2), (3, 0), (5, 2))]
-    checks.append(("a0", float(a0.grad),
+    # the same loss through the library's kernels only: GPU push, deposit, spectrum,
+    # lw_spectrum_grad and the forward-mode push gradient
+    u2 = torch.tensor(u0, device=dev, requires_grad=True)
+    a2 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
+    w2 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
+    S2 = PushSpectrum.apply(u2, a2, w2, torch.tensor(r0, device=dev), laser.lam, laser.fwhm,
+                            t0, t1, n_s, det, grid)
+    L2 = band_energy(S2, grid, torch.from_numpy(mask))
+    L2.backward()
+    torch.cuda.synchronize()
+    assert abs(float(L2) / float(L) - 1.0) < 1e-9
+    assert float(torch.linalg.norm(u2.grad - u.grad) / torch.linalg.norm(u.grad)) < 1e-7
+    checks = [(f"u0[{k},{c}]", (float(u.grad[k, c]), float(u2.grad[k, c])),
+               kink_free_fd(shift_u(k, c), gamma)) for (k, c) in ((0, 2), (3, 0), (5, 2))]
+    checks.append(("a0", (float(a0.grad), float(a2.grad)),
                    kink_free_fd(lambda h: (u0, laser.a0 + h, laser.w0), laser.a0)))
-    checks.append(("w0", float(w0.grad),
+    checks.append(("w0", (float(w0.grad), float(w2.grad)),
                    kink_free_fd(lambda h: (u0, laser.a0, laser.w0 + h), laser.w0)))
-    for name, g, fd in checks:
-        assert abs(g - fd) <= TOL * abs(fd), (name, g, fd)
+    for name, gs, fd in checks:
+        for g in gs:   # torch-autograd pusher, then the library's forward-mode kernel
+            assert abs(g - fd) <= TOL * abs(fd), (name, g, fd)

@@ -106,6 +106,18 @@ def c4_grad(n_e=2048, n_s=4096, nx=32, n_bins=16_384) -> Workload:
                     half_angle_g=1.0, laser=laser, eps_n=0.0)
 
 
+def c4_setup(n_e=2048, n_s=4096, nx=32, n_bins=16_384):
+    """Initial state of config 4 without pushing it: (r0, u0, laser, t_start, t_end, n_s,
+    n_hat, n_bins, gamma) -- the same bunch and laser as c4_grad."""
+    laser = GaussianLaser(lam=1e-6, a0=1.0, w0=20e-6, fwhm=10e-15)
+    gamma = 60.0
+    env = laser.sigma * np.sqrt(2.0 * np.log(1e6))
+    t_half = 0.5 * env * 1.05
+    r0, u0 = gaussian_bunch(n_e, SEED_BASE + 4, 0.0, 0.0, 0.0, gamma, 1e-3, 0.0, -t_half)
+    n_hat, _, _ = detector_grid(nx, nx, 1.0 / gamma)
+    return r0, u0, laser, -t_half, t_half, n_s, n_hat, n_bins, gamma
+
+
 def c5_batch(n_variants=64, seed=SEED_BASE + 5, n_e=(512, 8192), n_s=(2000, 40000),
              nx=(16, 128), log2_bins=(12, 17), gamma=(20.0, 200.0), a0=(0.05, 1.0)):
     """Batched design sweep: independent variants with gamma log-uniform, a0 uniform,
