@@ -787,6 +787,87 @@ def run_c4(args):
             "torch_pusher": ref}
 
 
+# ----------------------------------------------------------------------------- TDM vs FDM
+
+def run_fdm(args):
+    """The time-domain path against the frequency-domain direct sum (Eq. inty_dft,
+    Algorithm 1) on a Nyquist-resolved C2 bunch at the C2 electron and step counts
+    (10,000 electrons x 10,000 Boris steps; sigma_z = 0.1 um, sigma_x = sigma_y = 0.5 um so
+    that 2^17 bins resolve the second harmonic) on 256 pixels over +-1.5/gamma and 2,048
+    frequencies over 0.2 .. 2.5 omega_1: the normalised error of Eq. spectra_error (mean,
+    max) of the mixed and FP64 time-domain spectra against the FDM, the FDM against the CPU
+    oracle's FDM on sampled pixels and frequencies, and the FDM's throughput in terms
+    N_s N_p N_obs N_omega per second."""
+    import torch
+
+    import oracle
+    from paper_2206_03015_gb300 import lw
+    from workloads import configs
+    from workloads.planewave import doppler_fundamental
+
+    dev = torch.device("cuda", 0)
+    w = configs.c2x(n_e=args.fdm_ne, n_s=args.fdm_ns, nx=16, n_bins=1 << 17)
+    tr = w.traj
+    ins = [torch.from_numpy(x).to(dev) for x in (tr.t, tr.r, tr.beta, tr.beta_dot)]
+    det = lw.Detector(w.n_hat, device=dev)
+    traj = lw.lw_trajectories_upload(*ins, sections=lw.LW_SECTION_FP64 | lw.LW_SECTION_MIXED,
+                                     device=dev)
+    bnd = lw.lw_grid_bounds(traj, det).cpu().numpy()
+    grid = lw.grid_from_bounds(bnd[0], bnd[1], w.n_bins)
+    d_omega = 2 * math.pi / (grid.n_bins * grid.dt_u)
+    w1 = doppler_fundamental(w.gamma, w.lam, w.a0)
+    n_om = args.fdm_nomega
+    l0 = int(round(0.2 * w1 / d_omega))
+    step = max(1, int(round(2.3 * w1 / d_omega / n_om)))   # FDM frequencies on TDM bins
+    om0, dom = l0 * d_omega, step * d_omega
+    dt = float(tr.t[1] - tr.t[0])
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    S_f, ms_f = timed(lambda: lw.lw_spectrum_fdm(traj, det, om0, dom, n_om, dt))
+    cols = torch.arange(n_om, device=dev) * step + l0
+    res = {}
+    for name, prec in (("tdm_mixed", lw.LW_MIXED_F32X4), ("tdm_fp64", lw.LW_FP64)):
+        def tdm():
+            rec = lw.lw_deposit_time_domain(traj, det, grid, prec)
+            return lw.lw_spectrum(rec, prec, det.n_pix, grid)
+        S_t, ms_t = timed(tdm)
+        err = (S_t.double()[:, cols] - S_f).abs() / S_f.max()
+        res[name] = {"ms": ms_t, "deposits_per_s": tr.n_e * tr.n_s * det.n_pix / (ms_t * 1e-3),
+                     "spectra_error_mean": float(err.mean()), "spectra_error_max": float(err.max())}
+    # the GPU FDM against the oracle's FDM: 2 pixels x 8 frequencies, all electrons and samples
+    pix = [0, det.n_pix // 2 + 8]
+    fi = np.linspace(0, n_om - 1, 8).astype(np.int64)
+    om = om0 + dom * fi
+    t0 = time.time()
+    S_o, _ = oracle.fdm(tr.t, tr.r, tr.beta, tr.beta_dot, w.n_hat[pix], om, dt)
+    cpu_s = time.time() - t0
+    S_g = S_f[pix][:, fi.tolist()].cpu().numpy()
+    terms = tr.n_e * (tr.n_s + 1) * det.n_pix * n_om
+    return {"metric": "FDM terms/s (electron.sample.pixel.frequency), Eq. inty_dft",
+            "value": terms / (ms_f * 1e-3), "unit": "terms/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"c2x at C2 counts: {tr.n_e} electrons x {tr.n_s} Boris steps "
+                                   f"(sigma_z 0.1 um, sigma_x,y 0.5 um), {det.n_pix} pixels over "
+                                   f"+-1.5/gamma, {w.n_bins} bins; FDM on {n_om} frequencies "
+                                   f"{om0 / w1:.2f} .. {(om0 + dom * (n_om - 1)) / w1:.2f} omega_1",
+                       "omega_1": w1},
+            "tdm_vs_fdm": res,
+            "fdm_vs_oracle_rel_l2": float(np.linalg.norm(S_g - S_o) / np.linalg.norm(S_o)),
+            "oracle_sample": {"pixels": pix, "frequencies": len(fi), "cpu_s": cpu_s,
+                              "cores": oracle.num_threads()}}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -857,7 +938,10 @@ def main():
     ap.add_argument("--shard", default="pixels", choices=["pixels", "detectors"],
                     help="N > 1: split one detector's pixels (strong scaling) or give each "
                          "rank a detector of its own (weak scaling)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "fdm"])
+    ap.add_argument("--fdm-ne", type=int, default=10_000)
+    ap.add_argument("--fdm-ns", type=int, default=10_000)
+    ap.add_argument("--fdm-nomega", type=int, default=2048)
     ap.add_argument("--c4-ne", type=int, default=2048)
     ap.add_argument("--c4-ns", type=int, default=4096)
     ap.add_argument("--c4-nx", type=int, default=32)
@@ -886,6 +970,8 @@ def main():
         res = run_c5(args)
     elif args.workload == "c4":
         res = run_c4(args)
+    elif args.workload == "fdm":
+        res = run_fdm(args)
     else:
         res = run_ours(args, rank, world, dist)
     if rank == 0 and res is not None:
