@@ -577,9 +577,11 @@ def cpu_baseline(w, grid, S_gpu, args):
 # ----------------------------------------------------------------------------- C5 sweep
 
 def run_c5(args):
-    """Batched design sweep: all variants' deposits in one persistent launch and their
-    spectra, captured in one CUDA graph, against the same work launched variant by
-    variant; tile shapes from the autotuner."""
+    """Batched design sweep (config 5): every variant's trajectories pushed on the GPU
+    (lw_boris_push from its bunch), uploaded, tile shapes from the autotuner; then, wave by
+    wave (as many variants as the memory budget holds), one persistent deposit launch and
+    the variants' spectra captured in one CUDA graph and replayed as the timed step, against
+    the same work launched variant by variant.  A step is every wave once."""
     import torch
 
     from paper_2206_03015_gb300 import lw
@@ -587,84 +589,127 @@ def run_c5(args):
     from workloads import configs
 
     dev = torch.device("cuda", 0)
+    PREC = {"f32": lw.LW_MIXED_F32, "x4": lw.LW_MIXED_F32X4, "f64": lw.LW_MIXED}[args.c5_record]
     vs = configs.c5_batch(n_variants=args.c5_variants, n_e=(args.c5_ne[0], args.c5_ne[1]),
                           n_s=(args.c5_ns[0], args.c5_ns[1]), nx=(args.c5_nx[0], args.c5_nx[1]),
                           log2_bins=(args.c5_bins[0], args.c5_bins[1]))
-    t0 = time.time()
-    items = []
     tuner = Autotuner(reps=1)
-    for v in vs:
-        w = v.build()
-        tr = w.traj
-        inputs = tuple(torch.from_numpy(x).to(dev) for x in (tr.t, tr.r, tr.beta, tr.beta_dot))
-        det = lw.Detector(w.n_hat, device=dev)
-        traj = lw.lw_trajectories_upload(*inputs, sections=lw.LW_SECTION_MIXED, device=dev)
-        b = lw.lw_grid_bounds(traj, det).cpu().numpy()
-        grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
-        choice = tuner.tune(inputs, det, grid, blocks=(128, 256, 512), chunks=(1, 2, 4, 8, 16))
-        traj = lw.lw_trajectories_upload(*inputs, sections=lw.LW_SECTION_MIXED,
+    rec_word = {lw.LW_MIXED_F32: 12, lw.LW_MIXED_F32X4: 16, lw.LW_MIXED: 24}[PREC]
+
+    def resident_bytes(v):   # mixed section + record + spectrum of one variant
+        return (v.n_e * (v.n_s + 1) * 40 + v.nx * v.nx * v.n_bins * rec_word
+                + v.nx * v.nx * (v.n_bins // 2 + 1) * 4)
+
+    # waves: variants by decreasing work, each wave filled up to the budget
+    order = sorted(range(len(vs)), key=lambda i: -vs[i].deposits)
+    budget = args.c5_budget_gb * 1e9
+    waves, cur, used = [], [], 0.0
+    for i in order:
+        b = resident_bytes(vs[i])
+        if cur and used + b > budget:
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(i)
+        used += b
+    if cur:
+        waves.append(cur)
+
+    def build(v):
+        r0, u0, t0, t1, n_hat = v.initial_state()
+        dt = (t1 - t0) / v.n_s
+        t = torch.empty(v.n_s + 1, dtype=torch.float64, device=dev)
+        R, B, A = (torch.empty((v.n_e, v.n_s + 1, 3), dtype=torch.float64, device=dev)
+                   for _ in range(3))
+        L = (v.laser.lam, v.laser.a0, v.laser.w0, v.laser.fwhm)
+        lw.lw_boris_push(torch.from_numpy(r0).to(dev), torch.from_numpy(u0).to(dev), t0, dt,
+                         v.n_s, L, t, R, B, A)
+        det = lw.Detector(n_hat, device=dev)
+        traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_MIXED, device=dev)
+        bnd = lw.lw_grid_bounds(traj, det).cpu().numpy()
+        grid = lw.grid_from_bounds(bnd[0], bnd[1], v.n_bins)
+        choice = tuner.tune((t, R, B, A), det, grid, blocks=tuple(args.c5_tune_blocks),
+                            chunks=tuple(args.c5_tune_chunks), precision=PREC)
+        traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_MIXED,
                                          block=choice.block, device=dev)
-        shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
-        rec = torch.empty(shp, dtype=dt, device=dev)
-        S = torch.empty((det.n_pix, grid.n_bins // 2 + 1), dtype=torch.float32, device=dev)
-        ws = lw.workspace(lw.spectrum_workspace_bytes(lw.LW_MIXED, det.n_pix, grid), dev)
-        items.append(dict(w=w, traj=traj, det=det, grid=grid, rec=rec, S=S, ws=ws,
-                          choice=choice, deposits=w.deposits))
-        del inputs
-    t_setup = time.time() - t0
-    bp = lw.lw_batch_plan([i["traj"] for i in items], [i["det"] for i in items],
-                          [i["grid"] for i in items], [i["rec"] for i in items],
-                          e_chunks=[i["choice"].e_chunk for i in items])
+        del t, R, B, A
+        return dict(traj=traj, det=det, grid=grid, choice=choice, v=v)
 
-    def batched():
-        lw.lw_batch_deposit(bp)
-        for i in items:
-            lw.lw_spectrum(i["rec"], lw.LW_MIXED, i["det"].n_pix, i["grid"], ws=i["ws"],
-                           out=i["S"])
-
-    def sequential():
-        for i in items:
-            lw.lw_deposit_time_domain(i["traj"], i["det"], i["grid"], lw.LW_MIXED,
-                                      record=i["rec"])
-            lw.lw_spectrum(i["rec"], lw.LW_MIXED, i["det"].n_pix, i["grid"], ws=i["ws"],
-                           out=i["S"])
-
-    batched()
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    st = torch.cuda.Stream()
-    st.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(st):
-        with torch.cuda.graph(g, stream=st):
-            batched()
-    torch.cuda.current_stream().wait_stream(st)
-
-    def timed(fn):
-        for _ in range(args.warmup):
+    def timed(fn, reps, warm):
+        for _ in range(warm):
             fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(reps):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / reps
 
-    ms_graph = timed(g.replay)
-    ms_seq = timed(sequential)
-    dep = sum(i["deposits"] for i in items)
+    t_setup = time.time()
+    ms_graph = ms_seq = 0.0
+    units, tiles, dep = 0, [], 0
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    for wave in waves:
+        items = [build(vs[i]) for i in wave]
+        for it in items:
+            shp, dt_ = lw.record_shape(it["det"], it["grid"], PREC)
+            it["rec"] = torch.empty(shp, dtype=dt_, device=dev)
+            it["S"] = torch.empty((it["det"].n_pix, it["grid"].n_bins // 2 + 1),
+                                  dtype=torch.float32, device=dev)
+        ws = lw.workspace(max(lw.spectrum_workspace_bytes(PREC, it["det"].n_pix, it["grid"])
+                              for it in items), dev)
+        bp = lw.lw_batch_plan([i["traj"] for i in items], [i["det"] for i in items],
+                              [i["grid"] for i in items], [i["rec"] for i in items],
+                              precision=PREC, statuses=[status] * len(items),
+                              e_chunks=[i["choice"].e_chunk for i in items])
+
+        def batched():
+            lw.lw_batch_deposit(bp)
+            for i in items:
+                lw.lw_spectrum(i["rec"], PREC, i["det"].n_pix, i["grid"], ws=ws, out=i["S"])
+
+        def sequential():
+            for i in items:
+                lw.lw_deposit_time_domain(i["traj"], i["det"], i["grid"], PREC, record=i["rec"],
+                                          status=status)
+                lw.lw_spectrum(i["rec"], PREC, i["det"].n_pix, i["grid"], ws=ws, out=i["S"])
+
+        batched()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                batched()
+        torch.cuda.current_stream().wait_stream(st)
+        ms_graph += timed(g.replay, args.steps, args.warmup)
+        ms_seq += timed(sequential, args.steps, min(args.warmup, 1))
+        units += bp.plan.n_units
+        tiles += [[i["choice"].block, i["choice"].e_chunk] for i in items]
+        dep += sum(i["v"].deposits for i in items)
+        del items, bp, g, ws
+        torch.cuda.empty_cache()
+    t_setup = time.time() - t_setup
+    torch.cuda.synchronize()
     return {"metric": METRIC, "value": dep / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": f"c5 sweep: {len(items)} variants, one persistent deposit "
-                                   f"launch + spectra in one CUDA graph",
-                       "deposits_per_step": dep, "units": bp.plan.n_units,
-                       "setup_s": round(t_setup, 1),
-                       "tiles": [[i["choice"].block, i["choice"].e_chunk] for i in items]},
-            "sequential": {"value": dep / (ms_seq * 1e-3), "ms_per_step": ms_seq}}
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"c5 sweep: {len(vs)} variants (gamma log-uniform 20-200, a0 "
+                                   f"0.05-1, {args.c5_ne[0]}-{args.c5_ne[1]} electrons, "
+                                   f"{args.c5_ns[0]}-{args.c5_ns[1]} steps, "
+                                   f"{args.c5_nx[0]}^2-{args.c5_nx[1]}^2 pixels, "
+                                   f"2^{args.c5_bins[0]}-2^{args.c5_bins[1]} bins), per wave one "
+                                   "persistent deposit launch + spectra in one CUDA graph",
+                       "deposits_per_step": dep, "units": units, "waves": len(waves),
+                       "wave_sizes": [len(w) for w in waves], "budget_gb": args.c5_budget_gb,
+                       "record": args.c5_record, "setup_s": round(t_setup, 1),
+                       "tiles": tiles},
+            "sequential": {"value": dep / (ms_seq * 1e-3), "ms_per_step": ms_seq},
+            "status": int(status.item())}
 
 
 # ----------------------------------------------------------------------------- C4 gradient
@@ -948,10 +993,14 @@ def main():
     ap.add_argument("--c4-bins", type=int, default=16_384)
     ap.add_argument("--no-torch-pusher", action="store_true")
     ap.add_argument("--c5-variants", type=int, default=64)
-    ap.add_argument("--c5-ne", type=int, nargs=2, default=(128, 1024))
-    ap.add_argument("--c5-ns", type=int, nargs=2, default=(2000, 8000))
-    ap.add_argument("--c5-nx", type=int, nargs=2, default=(16, 64))
-    ap.add_argument("--c5-bins", type=int, nargs=2, default=(12, 16))
+    ap.add_argument("--c5-ne", type=int, nargs=2, default=(512, 8192))
+    ap.add_argument("--c5-ns", type=int, nargs=2, default=(2000, 40000))
+    ap.add_argument("--c5-nx", type=int, nargs=2, default=(16, 128))
+    ap.add_argument("--c5-bins", type=int, nargs=2, default=(12, 17))
+    ap.add_argument("--c5-record", default="f32", choices=["f32", "x4", "f64"])
+    ap.add_argument("--c5-budget-gb", type=float, default=200.0)
+    ap.add_argument("--c5-tune-blocks", type=int, nargs="+", default=(256, 512))
+    ap.add_argument("--c5-tune-chunks", type=int, nargs="+", default=(1, 4))
     args = ap.parse_args()
     args.full = (args.n_e, args.n_s, args.nx, args.n_bins) == (10_000, 10_000, 64, 65_536)
     world = _env_int("WORLD_SIZE", 1)

@@ -47,8 +47,9 @@ class Autotuner:
                 json.dump(self.cache, f, indent=1, sort_keys=True)
             os.replace(tmp, self.cache_path)
 
-    def _time(self, traj, det, grid, record, e_chunk):
-        bp = lw.lw_batch_plan([traj], [det], [grid], [record], e_chunks=[e_chunk])
+    def _time(self, traj, det, grid, record, e_chunk, precision=lw.LW_MIXED):
+        bp = lw.lw_batch_plan([traj], [det], [grid], [record], precision=precision,
+                              e_chunks=[e_chunk])
         lw.lw_batch_deposit(bp)                       # warm-up
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -59,14 +60,16 @@ class Autotuner:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / self.reps
 
-    def tune(self, inputs, det, grid, blocks=BLOCKS, chunks=CHUNKS) -> Choice:
-        """inputs: (t, r, beta, beta_dot) device tensors of one variant."""
+    def tune(self, inputs, det, grid, blocks=BLOCKS, chunks=CHUNKS,
+             precision=lw.LW_MIXED) -> Choice:
+        """inputs: (t, r, beta, beta_dot) device tensors of one variant; precision: the
+        mixed record the batch will use."""
         n_e, ns1, _ = inputs[1].shape
-        key = shape_key(n_e, ns1 - 1, det.n_pix, grid.n_bins)
+        key = shape_key(n_e, ns1 - 1, det.n_pix, grid.n_bins) + f"/{precision}"
         if key in self.cache:
             c = self.cache[key]
             return Choice(c["block"], c["e_chunk"], c["ms"])
-        shp, dt = lw.record_shape(det, grid, lw.LW_MIXED)
+        shp, dt = lw.record_shape(det, grid, precision)
         record = torch.empty(shp, dtype=dt, device=det.n_hat.device)
         best = None
         for block in blocks:
@@ -75,7 +78,7 @@ class Autotuner:
             for ch in chunks:
                 if ch > n_e:
                     continue
-                ms = self._time(traj, det, grid, record, ch)
+                ms = self._time(traj, det, grid, record, ch, precision)
                 if best is None or ms < best.ms:
                     best = Choice(block, ch, ms)
         self.cache[key] = {"block": best.block, "e_chunk": best.e_chunk, "ms": best.ms}

@@ -162,3 +162,13 @@ class _LazyVariant:
     def build(self) -> Workload:
         return _c2_like(self.name, self.n_e, self.n_s, self.nx, self.n_bins, 5e-6, 5e-6, 10e-6,
                         self.seed, laser=self.laser, gamma=self.gamma)
+
+    def initial_state(self):
+        """What build() pushes, without pushing it: (r0, u0, t_start, t_end, n_hat) -- the
+        same bunch, time window and detector, for a pusher of the caller's choice."""
+        env = self.laser.sigma * np.sqrt(2.0 * np.log(1e6))
+        t_half = 0.5 * (env + 4.0 * 10e-6 / C0) * 1.05
+        r0, u0 = gaussian_bunch(self.n_e, self.seed, 5e-6, 5e-6, 10e-6, self.gamma, 1e-3,
+                                0.5e-6, -t_half)
+        n_hat, _, _ = detector_grid(self.nx, self.nx, 1.5 / self.gamma)
+        return r0, u0, -t_half, t_half, n_hat
