@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     dft,
     spectrum,
     fdm,
+    tdm_grad,
     num_threads,
     FLAG_ACCEL,
     FLAG_VELOCITY,

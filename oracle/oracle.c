@@ -165,6 +165,31 @@ static int finite3(const double *v) {
 /* Bounds of the uniform observer grid, Eqs. (tu_min) and (tu_max):
  *   t_u^min = min over (k, m) of t_a^{k,m}(t_start),
  *   t_u^max = max over (k, m) of t_a^{k,m}(t_end). */
+/* Step 3-4 of oracle_tdm_grad for one sample: dL/d(r, beta, beta_dot) added from
+ * dL/dE (gE) and dL/dt_a (gta) of the sample, E its far acceleration field. */
+static void field_gradient(const double *n, const double *b, const double *a, const double *E,
+                           const double *gE, double gta, double *o_r, double *o_b, double *o_a) {
+    for (int d = 0; d < 3; ++d) o_r[d] += -gta * n[d] / OR_C0;
+    const double D = 1.0 - dot3(n, b);
+    if (!(dot3(b, b) < 1.0) || !(D > 0.0)) return;
+    const double D3 = D * D * D;
+    const double nmb[3] = {n[0] - b[0], n[1] - b[1], n[2] - b[2]};
+    for (int d = 0; d < 3; ++d) {
+        double e[3] = {0.0, 0.0, 0.0}, inner[3], dE[3];
+        e[d] = 1.0;
+        /* dE/dbeta_dot_d = n x ((n - beta) x e_d) / D^3 */
+        cross3(nmb, e, inner);
+        cross3(n, inner, dE);
+        o_a[d] += (gE[0] * dE[0] + gE[1] * dE[1] + gE[2] * dE[2]) / D3;
+        /* dE/dbeta_d = n x (-e_d x beta_dot) / D^3 + 3 n_d E / D */
+        cross3(e, a, inner);
+        cross3(n, inner, dE);
+        double s = -(gE[0] * dE[0] + gE[1] * dE[1] + gE[2] * dE[2]) / D3;
+        s += 3.0 * n[d] * dot3(gE, E) / D;
+        o_b[d] += s;
+    }
+}
+
 int oracle_grid_bounds(int64_t n_e, int64_t n_s, const double *t, int t_per_electron,
                        const double *r, const double *beta, const double *beta_dot,
                        int64_t n_pix, const double *n_hat, double R, int flags,
@@ -395,6 +420,129 @@ int oracle_spectrum(int64_t n_pix, int64_t n_bins, const double *rec, double dt_
         free(im);
     }
     return 0;
+}
+
+/* Gradient of L = sum_m sum_{l=0}^{N/2} g[m][l] S[m][l] (S as oracle_spectrum with charge q)
+ * of the far acceleration field's spectra, with respect to every sample's r, beta and
+ * beta_dot (added to dr, dbeta, dbdot [n_e][n_s+1][3]), by the chain rule written out:
+ *  1. the record of oracle_tdm_deposit (Algorithm 2) and its DFT X (Eq. efield_xfrom),
+ *     S = K dt_u^2 sum_c |X_c|^2 (Eq. const_phase_drop), so
+ *     dL/drec_c[j] = K dt_u^2 sum_{l=0}^{N/2} g_l 2 Re(conj(X_c(l)) exp(+2 pi i j l / N))
+ *     (a direct sum over l);
+ *  2. Algorithm 2's value at grid point t_j of the step (t_b, t_a],
+ *     E_b (t_a - t_j)/(t_a - t_b) + E_a (t_j - t_b)/(t_a - t_b), differentiated with
+ *     respect to E_b, E_a, t_a and t_b;
+ *  3. t_a = t - n.r / c0 (Eq. far_adv): dL/dr = -(dL/dt_a) n / c0;
+ *  4. E = n x ((n - beta) x beta_dot) / D^3, D = 1 - n.beta (Eq. far_efield):
+ *     dE/dbeta_dot_d = n x ((n - beta) x e_d) / D^3,
+ *     dE/dbeta_d = n x (-e_d x beta_dot) / D^3 + 3 n_d E / D
+ *     (e_d the unit vector d), each applied with the cross products literally.
+ * Samples with |beta| >= 1 or D <= 0 carry no field and get no field gradient. */
+int oracle_tdm_grad(int64_t n_e, int64_t n_s, const double *t, int t_per_electron,
+                    const double *r, const double *beta, const double *beta_dot,
+                    int64_t n_pix, const double *n_hat, double t_min, double dt_u,
+                    int64_t n_bins, const double *g, double q, double *dr, double *dbeta,
+                    double *dbdot) {
+    if (n_bins < 2 || (n_bins & (n_bins - 1))) return -1;
+    or_traj tr = {n_e, n_s, t, t_per_electron, r, beta, beta_dot};
+    const int64_t nl = n_bins / 2 + 1;
+    const double K = q * q / (16.0 * OR_PI * OR_PI * OR_PI * OR_EPS0 * OR_C0);
+    const double scale = K * dt_u * dt_u;
+    const double inv_dt_u = 1.0 / dt_u;
+    const size_t n_rec = (size_t)(n_pix * 3 * n_bins);
+    double *rec = (double *)malloc(sizeof(double) * n_rec);
+    double *drec = (double *)malloc(sizeof(double) * n_rec);
+    int st = 0;
+    oracle_tdm_deposit(n_e, n_s, t, t_per_electron, r, beta, beta_dot, n_pix, n_hat, 1.0, t_min,
+                       dt_u, n_bins, FLAG_ACCEL, 0, rec, &st);
+    /* step 1: dL/drec by direct sums */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t row = 0; row < n_pix * 3; ++row) {
+        const int64_t m = row / 3;
+        const double *x = rec + row * n_bins;
+        double *Xre = (double *)malloc(sizeof(double) * (size_t)nl);
+        double *Xim = (double *)malloc(sizeof(double) * (size_t)nl);
+        for (int64_t l = 0; l < nl; ++l) {
+            double re = 0.0, im = 0.0;
+            for (int64_t j = 0; j < n_bins; ++j) {
+                double ang = 2.0 * OR_PI * (double)((j * l) % n_bins) / (double)n_bins;
+                re += x[j] * cos(ang);
+                im += x[j] * sin(ang);
+            }
+            Xre[l] = re;
+            Xim[l] = im;
+        }
+        for (int64_t j = 0; j < n_bins; ++j) {
+            double acc = 0.0;
+            for (int64_t l = 0; l < nl; ++l) {
+                double ang = 2.0 * OR_PI * (double)((j * l) % n_bins) / (double)n_bins;
+                /* Re(conj(X) e^{i ang}) = Xre cos + Xim sin */
+                acc += g[m * nl + l] * 2.0 * (Xre[l] * cos(ang) + Xim[l] * sin(ang));
+            }
+            drec[row * n_bins + j] = scale * acc;
+        }
+        free(Xre);
+        free(Xim);
+    }
+    /* steps 2-4, electron by electron (each writes only its own samples) */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n_e; ++k) {
+        for (int64_t m = 0; m < n_pix; ++m) {
+            const double *n = n_hat + 3 * m;
+            const double *R = drec + m * 3 * n_bins;
+            double tb = 0.0, Eb[3] = {0.0, 0.0, 0.0};
+            double gEb[3] = {0.0, 0.0, 0.0}, gtb = 0.0;   /* dL/d(E, t_a) of sample i-1 */
+            for (int64_t i = 0; i <= n_s; ++i) {
+                const double *xi = tr_vec(r, &tr, k, i);
+                const double *bi = tr_vec(beta, &tr, k, i);
+                const double *ai = tr_vec(beta_dot, &tr, k, i);
+                const double ta = advanced_time_far(n, xi, tr_time(&tr, k, i));
+                double E[3];
+                lw_field(n, 1.0, FLAG_ACCEL, xi, bi, ai, E);
+                double gE[3] = {0.0, 0.0, 0.0}, gta = 0.0;   /* sample i */
+                if (i > 0) {
+                    const double ua = (ta - t_min) * inv_dt_u, ub = (tb - t_min) * inv_dt_u;
+                    if (fabs(ua) < 4.0e18 && fabs(ub) < 4.0e18) {
+                        int64_t a = (int64_t)floor(ub) + 1, z = (int64_t)floor(ua);
+                        if (a < 0) a = 0;
+                        if (z > n_bins - 1) z = n_bins - 1;
+                        const double den = ta - tb;
+                        for (int64_t j = a; j <= z; ++j) {
+                            const double tu = t_min + (double)j * dt_u;
+                            for (int c = 0; c < 3; ++c) {
+                                const double Rc = R[c * n_bins + j];
+                                gEb[c] += Rc * (ta - tu) / den;
+                                gE[c] += Rc * (tu - tb) / den;
+                                /* d/dt_a and d/dt_b of Eb (ta-tu)/den + E (tu-tb)/den */
+                                gta += Rc * (Eb[c] - E[c]) * (tu - tb) / (den * den);
+                                gtb += Rc * (Eb[c] - E[c]) * (ta - tu) / (den * den);
+                            }
+                        }
+                    }
+                    /* sample i-1 is complete */
+                    double *o_r = dr + 3 * (k * (n_s + 1) + i - 1);
+                    double *o_b = dbeta + 3 * (k * (n_s + 1) + i - 1);
+                    double *o_a = dbdot + 3 * (k * (n_s + 1) + i - 1);
+                    field_gradient(n, tr_vec(beta, &tr, k, i - 1), tr_vec(beta_dot, &tr, k, i - 1),
+                                   Eb, gEb, gtb, o_r, o_b, o_a);
+                }
+                tb = ta;
+                for (int c = 0; c < 3; ++c) {
+                    Eb[c] = E[c];
+                    gEb[c] = gE[c];
+                }
+                gtb = gta;
+            }
+            double *o_r = dr + 3 * (k * (n_s + 1) + n_s);
+            double *o_b = dbeta + 3 * (k * (n_s + 1) + n_s);
+            double *o_a = dbdot + 3 * (k * (n_s + 1) + n_s);
+            field_gradient(n, tr_vec(beta, &tr, k, n_s), tr_vec(beta_dot, &tr, k, n_s), Eb, gEb,
+                           gtb, o_r, o_b, o_a);
+        }
+    }
+    free(rec);
+    free(drec);
+    return st;
 }
 
 /* Frequency-domain method, Eq. (inty_dft) / Algorithm 1:

@@ -60,9 +60,10 @@ def _configure(lib):
     lib.oracle_dft.argtypes = [I64, P, P, P, P]
     lib.oracle_spectrum.argtypes = [I64, I64, P, D, D, P, P]
     lib.oracle_fdm.argtypes = [I64, I64, P, I, P, P, P, I64, P, I64, P, D, D, P]
+    lib.oracle_tdm_grad.argtypes = [I64, I64, P, I, P, P, P, I64, P, D, D, I64, P, D, P, P, P]
     for f in ("oracle_grid_bounds", "oracle_advanced_times", "oracle_fields",
               "oracle_tdm_deposit", "oracle_fft", "oracle_dft", "oracle_spectrum",
-              "oracle_fdm", "oracle_num_threads"):
+              "oracle_fdm", "oracle_tdm_grad", "oracle_num_threads"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -246,6 +247,21 @@ def fdm(t, r, beta, beta_dot, n_hat, omega, dt, q=Q_E):
                         _ptr(tr.beta_dot), n_hat.shape[0], _ptr(n_hat), omega.shape[0],
                         _ptr(omega), float(dt), float(q), _ptr(S))
     return S, st
+
+
+def tdm_grad(t, r, beta, beta_dot, n_hat, t_min, dt_u, n_bins, g, q=Q_E):
+    """Gradient of L = sum g[m][l] S[m][l] (acceleration far field, l = 0..n_bins/2) with
+    respect to every sample's r, beta, beta_dot: (dr, dbeta, dbdot) [n_e][n_s+1][3]."""
+    lib = load()
+    tr = _Traj(t, r, beta, beta_dot)
+    n_hat = _f64(n_hat).reshape(-1, 3)
+    g = _f64(g).reshape(n_hat.shape[0], int(n_bins) // 2 + 1)
+    out = [np.zeros((tr.n_e, tr.n_s + 1, 3)) for _ in range(3)]
+    lib.oracle_tdm_grad(tr.n_e, tr.n_s, _ptr(tr.t), tr.t_per_e, _ptr(tr.r), _ptr(tr.beta),
+                        _ptr(tr.beta_dot), n_hat.shape[0], _ptr(n_hat), float(t_min),
+                        float(dt_u), int(n_bins), _ptr(g), float(q), _ptr(out[0]), _ptr(out[1]),
+                        _ptr(out[2]))
+    return tuple(out)
 
 
 def num_threads() -> int:

@@ -474,6 +474,46 @@ def pin_status_bits():
     assert st & oracle.ST_NONFINITE
 
 
+def pin_gradient_central_differences():
+    """The oracle's gradient of L = sum g S (oracle.tdm_grad) against central differences
+    of the oracle's own loss, per input element: position, velocity, acceleration of
+    samples (the four largest gradients of each array and one of median size), to 1e-3 of
+    the difference quotient (steps of 1e-6 of each array's scale; the loss is piecewise
+    smooth, so a stencil near a grid-point crossing measures the slope to about that)."""
+    tr = simple.random_smooth(3, 60, 2e-18, 301, gamma=5.0, amp=0.5)
+    n_hat = _rand_dirs(5, 7, 0.3)
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+    n_bins = 256
+    dt_u = (hi - lo) / 250
+    t_min = lo - 3 * dt_u
+    rng = np.random.Generator(np.random.PCG64(9))
+    g = rng.uniform(0.5, 1.5, size=(5, n_bins // 2 + 1))
+    grads = oracle.tdm_grad(tr.t, tr.r, tr.beta, tr.beta_dot, n_hat, t_min, dt_u, n_bins, g)
+
+    def loss(r, b, a):
+        rec, _ = oracle.tdm_deposit(tr.t, r, b, a, n_hat, t_min, dt_u, n_bins)
+        return float(np.sum(g * oracle.spectrum(rec, dt_u)))
+
+    base = [tr.r, tr.beta, tr.beta_dot]
+    for which in range(3):
+        h = 1e-6 * np.abs(base[which]).max()
+        ga = np.abs(grads[which])
+        gmax = ga.max()
+        assert gmax > 0
+        # the four largest elements and one of median size among the nonzero ones
+        flat = np.argsort(ga.ravel())
+        nz = flat[ga.ravel()[flat] > 0]
+        picks = list(flat[-4:]) + [nz[len(nz) // 2]]
+        for (k, i, c) in (np.unravel_index(f, ga.shape) for f in picks):
+            plus = [x.copy() for x in base]
+            minus = [x.copy() for x in base]
+            plus[which][k, i, c] += h
+            minus[which][k, i, c] -= h
+            fd = (loss(*plus) - loss(*minus)) / (2 * h)
+            assert abs(grads[which][k, i, c] - fd) <= 1e-3 * max(abs(fd), 1e-3 * gmax), \
+                (which, k, i, c, grads[which][k, i, c], fd)
+
+
 ALL_PINS = [
     pin_table1_tu_estimation,
     pin_table2_ntu_ratio,
@@ -495,4 +535,5 @@ ALL_PINS = [
     pin_coherence,
     pin_fdm_vs_tdm,
     pin_status_bits,
+    pin_gradient_central_differences,
 ]

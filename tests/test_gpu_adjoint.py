@@ -1,6 +1,7 @@
 """Adjoint (lw_spectrum_grad, FP64) against central finite differences of the
-CPU oracle, and the end-to-end gradient of a band-integrated spectral yield
-with respect to initial momenta and the laser a0 / waist (differentiable
+CPU oracle and against the oracle's own gradient, and the end-to-end gradient
+of a band-integrated spectral yield with respect to initial momenta and the
+laser a0 / waist (differentiable
 Boris pusher + LWSpectrum) against finite differences of the oracle fed by
 the workload generator's pusher.  Tolerance 1e-3 relative.
 
@@ -74,6 +75,34 @@ def test_spectrum_grad_matches_oracle_finite_differences():
                                                                   grads[which][k, i, c], fd)
             checked += 1
     assert checked == 12
+
+
+@pytest.mark.parametrize("t_per_electron", [False, True])
+def test_spectrum_grad_matches_oracle_gradient(t_per_electron):
+    """lw_spectrum_grad against the oracle's own gradient (the chain rule written out in
+    plain C, pinned by central differences of the oracle's loss), element by element: both
+    FP64 with the same interval decisions, so they agree to rounding (1e-9 of the largest
+    element)."""
+    tr = simple.random_smooth(4, 90, 2e-18, 41, gamma=6.0, amp=0.4,
+                              t_per_electron=t_per_electron)
+    n_hat = _dirs(7, 5, 0.25)
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+    grid = lw.Grid(lo - 2.5 * (hi - lo) / 500, (hi - lo) / 500, 512)
+    rng = np.random.Generator(np.random.PCG64(17))
+    w = rng.uniform(0.2, 2.0, size=(7, 257))
+    ref = oracle.tdm_grad(tr.t, tr.r, tr.beta, tr.beta_dot, n_hat, grid.t_min, grid.dt_u,
+                          grid.n_bins, w)
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot, sections=lw.LW_SECTION_FP64)
+    det = lw.Detector(n_hat)
+    rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
+    S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, want_X=True)
+    got = lw.lw_spectrum_grad(traj, det, grid, X, torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    for name, g, o in zip(("r", "beta", "beta_dot"), got, ref):
+        g = g.cpu().numpy()
+        assert np.abs(o).max() > 0, name
+        assert np.abs(g - o).max() <= 1e-9 * np.abs(o).max(), (name, np.abs(g - o).max(),
+                                                               np.abs(o).max())
 
 
 def _c4_small():

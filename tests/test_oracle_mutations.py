@@ -41,6 +41,13 @@ MUTATIONS = {
     "grid_min_at_end": ("if (a0 < lo) lo = a0;", "if (a1 < lo) lo = a1;"),
     "fdm_doppler_power": ("double a = A[c] / (D * D);", "double a = A[c] / D;"),
     "clip_silent": ("if (a < 0) { a = 0; st |= ST_CLIP; }", "if (a < 0) { a = 0; }"),
+    "grad_t_a_sign": ("gta += Rc * (Eb[c] - E[c]) * (tu - tb) / (den * den);",
+                      "gta -= Rc * (Eb[c] - E[c]) * (tu - tb) / (den * den);"),
+    "grad_weights_swapped": ("gEb[c] += Rc * (ta - tu) / den;", "gEb[c] += Rc * (tu - tb) / den;"),
+    "grad_doppler_term": ("s += 3.0 * n[d] * dot3(gE, E) / D;", "s += 2.0 * n[d] * dot3(gE, E) / D;"),
+    "grad_time_map_sign": ("o_r[d] += -gta * n[d] / OR_C0;", "o_r[d] += gta * n[d] / OR_C0;"),
+    "grad_conjugate": ("acc += g[m * nl + l] * 2.0 * (Xre[l] * cos(ang) + Xim[l] * sin(ang));",
+                       "acc += g[m * nl + l] * 2.0 * (Xre[l] * cos(ang) - Xim[l] * sin(ang));"),
 }
 
 
