@@ -55,6 +55,11 @@ struct DepositArgs {
     int64_t n_pix;
     double R;
     double t_min, dt_u, inv_dtu;
+    // FP32 constants of the mixed path, rounded once on the host: 1/dt_u, c0 dt_u (a pixel
+    // direction from its slope) and c0/R (velocity field).  Kernel parameters can be FMA
+    // operands directly; a value converted from the FP64 fields inside the kernel would
+    // be recomputed on the FP64 pipe wherever the compiler chooses not to keep it.
+    float s32, inv_sc, c0_over_R;
     int64_t n_bins;
     uint32_t flags;
     void* record;
@@ -529,9 +534,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wslot = warp * 32 * PIX;
-    const float s32 = (float)p.inv_dtu;
-    const float c0_over_R = (FL & LW_FIELD_VELOCITY) ? (float)(kC0 / p.R) : 0.0f;
-    const float inv_sc = (float)(kC0 * p.dt_u);   // direction from slope: n_x = -w_x c0 dt_u
+    const float s32 = p.s32;
+    const float c0_over_R = (FL & LW_FIELD_VELOCITY) ? p.c0_over_R : 0.0f;
+    const float inv_sc = p.inv_sc;   // direction from slope: n_x = -w_x c0 dt_u
     const int nb = (int)p.n_bins;
     const int64_t pix0 = tile * kSlots;
     unsigned act = 0;
@@ -1293,6 +1298,14 @@ BatchedKernel batched_kernel(int acc, uint32_t fl) {
            : acc == kAccF32X4 ? batched_kernel_fl<kAccF32X4>(fl) : batched_kernel_fl<kAccF64>(fl);
 }
 
+// The mixed path's FP32 constants from the FP64 grid and detector fields (each the FP32
+// rounding of its correctly rounded FP64 value).
+void set_fp32_constants(DepositArgs& a) {
+    a.s32 = (float)a.inv_dtu;
+    a.inv_sc = (float)(kC0 * a.dt_u);
+    a.c0_over_R = (float)(kC0 / a.R);
+}
+
 }  // namespace
 }  // namespace lw
 
@@ -1340,6 +1353,7 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     a.t_min = grid->t_min;
     a.dt_u = grid->dt_u;
     a.inv_dtu = 1.0 / grid->dt_u;
+    set_fp32_constants(a);
     a.n_bins = grid->n_bins;
     a.flags = field_flags;
     a.record = record;
@@ -1459,6 +1473,7 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
         a.t_min = it.grid.t_min;
         a.dt_u = it.grid.dt_u;
         a.inv_dtu = 1.0 / it.grid.dt_u;
+        set_fp32_constants(a);
         a.n_bins = it.grid.n_bins;
         a.flags = field_flags;
         a.record = it.record;
