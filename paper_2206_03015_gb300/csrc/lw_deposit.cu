@@ -330,20 +330,20 @@ __device__ __forceinline__ void accumulate(void* rec, int64_t idx, float v) {
     }
 }
 
-// Adds the three components (v0, v1, v2) of grid point j of pixel m.
+// Adds the three components (v0, v1, v2) of grid point j to the pixel row starting at
+// `row` (the pixel's [3][N] values, or its [N][4] floats for the interleaved record).
 template <int ACC>
-__device__ __forceinline__ void deposit3(void* rec, int64_t m, int64_t j, int64_t n_bins,
-                                         float v0, float v1, float v2) {
+__device__ __forceinline__ void deposit3_row(unsigned char* row, int j, int64_t n_bins,
+                                             float v0, float v1, float v2) {
     if (ACC == kAccF32X4) {
-        float* p = static_cast<float*>(rec) + ((m * n_bins + j) << 2);
+        float* p = reinterpret_cast<float*>(row + 16ull * (unsigned)j);
         asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v0),
                      "f"(v1), "f"(v2), "f"(0.0f)
                      : "memory");
     } else {
-        const int64_t idx = m * 3 * n_bins + j;
-        accumulate<ACC>(rec, idx, v0);
-        accumulate<ACC>(rec, idx + n_bins, v1);
-        accumulate<ACC>(rec, idx + 2 * n_bins, v2);
+        accumulate<ACC>(row, j, v0);
+        accumulate<ACC>(row, j + n_bins, v1);
+        accumulate<ACC>(row, j + 2 * n_bins, v2);
     }
 }
 
@@ -525,7 +525,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     // turn), so the job offsets s_kp are indexed lane-major, wslot + lane * PIX + q; the
     // per-slot data are indexed q-major, wslot + q * 32 + lane, so that a warp's accesses
     // to its own slots are contiguous.
-    __shared__ float4 s_wh[kSlots];                   // slope hi parts (w_x, w_y, w_z)
+    __shared__ float4 s_wh[kSlots];                   // slope hi parts (w_x, w_y, w_z), row
     __shared__ int4 s_job[kSlots];                    // block: I, f, x_end
     __shared__ int s_ja[kSlots];                      // block: first grid point
     __shared__ int s_kp[kSlots];                      // block: job offset (lane-major)
@@ -562,7 +562,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         const double sc = kInvC0 * p.inv_dtu;
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
-        s_wh[wslot + q * 32 + lane] = make_float4(wx.hi, wy.hi, wz.hi, 0.0f);
+        // .w: the pixel's row in the tile (bits of an unsigned), for the record address
+        s_wh[wslot + q * 32 + lane] =
+            make_float4(wx.hi, wy.hi, wz.hi, __uint_as_float(q * kMixThreads + threadIdx.x));
         wlo[q][0] = wx.lo;
         wlo[q][1] = wy.lo;
         wlo[q][2] = wz.lo;
@@ -572,11 +574,11 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     if (tile == 0 && chunk == 0 && threadIdx.x == 0 && p.input_status) bits |= *p.input_status;
     float err2 = 0.0f, val2 = 0.0f;   // CHECK: squared error estimates and squared values
 
-    // pixel (global index) of q-major slot `sl`
-    auto slot_pixel = [&](int sl) -> int64_t {
-        const int w = sl / (32 * PIX), r = sl % (32 * PIX);
-        return pix0 + (r / 32) * kMixThreads + w * 32 + r % 32;
-    };
+    // the tile's first record row; a pixel row is 4 * record_words bytes per grid point
+    const uint64_t row_bytes =
+        4ull * (ACC == kAccF32X4 ? 4 : ACC == kAccF32 ? 3 : 6) * (uint64_t)p.n_bins;
+    unsigned char* const tile_rec =
+        CHECK ? nullptr : static_cast<unsigned char*>(p.record) + (uint64_t)pix0 * row_bytes;
     auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
     // blocks with at least one step: ceil((ns1 - 1) / B)
     const int nbs = (int)((p.ns1 - 2) / B + 1);
@@ -864,7 +866,8 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     const float u0 = v0 * 0x1p-50f, u1 = v1 * 0x1p-50f, u2 = v2 * 0x1p-50f;
                     val2 = fmaf(u0, u0, fmaf(u1, u1, fmaf(u2, u2, val2)));
                 } else {
-                    deposit3<ACC>(p.record, slot_pixel(sl), j, p.n_bins, v0, v1, v2);
+                    deposit3_row<ACC>(tile_rec + (uint64_t)__float_as_uint(w.w) * row_bytes, j,
+                                      p.n_bins, v0, v1, v2);
                 }
             };
             // the warp's grid points: prefix sum of the runs over the warp's slots, and the
