@@ -268,18 +268,26 @@ struct PixelConst {
     float nx, ny, nz, omnz;   // direction and 1 - n_z (stable)
 };
 
+// rcp.approx.ftz.f32: the reciprocal to about 1 ulp, far below the FP32 field's own error
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Per-sample FP32 field in the stable form, for the field terms FL (LW_FIELD_* mask, a
 // compile-time constant); zero if D <= 0.
-// f: the sample's six field floats as three 8-byte-aligned pairs.
+// f: the sample's six field floats as three 8-byte-aligned pairs
+// (beta_x, beta_y), (beta_dot_x, beta_dot_y), (1 - beta_z, beta_dot_z).
 template <int FL>
 __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* __restrict__ f,
                                            float c0_over_R, float F[3]) {
     const float2 f01 = f[0], f23 = f[1], f45 = f[2];
-    const float bx = f01.x, by = f01.y, eps = f23.x;
-    const float ax = f23.y, ay = f45.x, az = f45.y;
+    const float bx = f01.x, by = f01.y, eps = f45.x;
+    const float ax = f23.x, ay = f23.y, az = f45.y;
     const float D = fmaf(-pc.ny, by, fmaf(-pc.nx, bx, fmaf(pc.nz, eps, pc.omnz)));
     const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
-    const float invD = __fdividef(1.0f, D);   // rcp.approx: 1 ulp, far below the FP32 field's own error
+    const float invD = rcp_approx(D);
     const float invD3 = invD * invD * invD;
     float F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
     if (FL & LW_FIELD_ACCEL) {
@@ -299,6 +307,36 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* _
     F[0] = ok ? F0 : 0.0f;
     F[1] = ok ? F1 : 0.0f;
     F[2] = ok ? F2 : 0.0f;
+}
+
+// One end of a step for the deposit, with Eq. far_efield expanded: since n . (n - beta) =
+// D, n x ((n - beta) x beta_dot) / D^3 = (k m - beta_dot) / D^2 with m = n - beta and
+// k = n . beta_dot / D; the velocity field adds c0/R (1 - beta^2) / D to k.  Returns
+// k m - beta_dot (x and y packed for the FP32x2 instructions, z) and the scale
+// weight / D^2 (zero if D <= 0), so that the interpolated value is t_a s_a + t_b s_b.
+template <int FL>
+__device__ __forceinline__ void end_terms(const PixelConst& pc, float2 nxy,
+                                          const float2* __restrict__ f, float c0_over_R,
+                                          float weight, float2& txy, float& tz, float& sc) {
+    const float2 b = f[0], a = f[1], ez = f[2];   // (bx, by), (ax, ay), (1 - bz, az)
+    const float D = fmaf(-pc.ny, b.y, fmaf(-pc.nx, b.x, fmaf(pc.nz, ez.x, pc.omnz)));
+    const float2 m = __ffma2_rn(b, make_float2(-1.0f, -1.0f), nxy);
+    const float mz = ez.x - pc.omnz;
+    const float invD = rcp_approx(D);
+    float k = 0.0f;
+    if (FL & LW_FIELD_ACCEL) k = fmaf(pc.nz, ez.y, fmaf(pc.ny, a.y, pc.nx * a.x)) * invD;
+    if (FL & LW_FIELD_VELOCITY) {
+        const float g2 = fmaf(-b.y, b.y, fmaf(-b.x, b.x, ez.x * (2.0f - ez.x)));   // 1 - beta^2
+        k = fmaf(c0_over_R * g2, invD, k);
+    }
+    if (FL & LW_FIELD_ACCEL) {
+        txy = __ffma2_rn(m, make_float2(k, k), make_float2(-a.x, -a.y));
+        tz = fmaf(mz, k, -ez.y);
+    } else {
+        txy = __fmul2_rn(m, make_float2(k, k));
+        tz = mz * k;
+    }
+    sc = D > 0.0f ? weight * (invD * invD) : 0.0f;
 }
 
 // Grid points of one pixel and block above which the owning lane deposits them
@@ -485,9 +523,10 @@ __device__ __forceinline__ float coord_mag(float4 w, float s, float4 sc) {
 // (1 - n_z) + n_z (1 - beta_z) + |n_x beta_x| + |n_y beta_y|, each rounded to about an ulp,
 // and enters the field as D^-3.
 __device__ __forceinline__ float fd_rel(const PixelConst& pc, const float2* __restrict__ f) {
-    const float2 f01 = f[0], f23 = f[1];
-    const float D = fmaf(-pc.ny, f01.y, fmaf(-pc.nx, f01.x, fmaf(pc.nz, f23.x, pc.omnz)));
-    const float mag = fabsf(pc.nx * f01.x) + fabsf(pc.ny * f01.y) + pc.omnz + pc.nz * f23.x;
+    const float2 f01 = f[0];
+    const float eps = f[2].x;
+    const float D = fmaf(-pc.ny, f01.y, fmaf(-pc.nx, f01.x, fmaf(pc.nz, eps, pc.omnz)));
+    const float mag = fabsf(pc.nx * f01.x) + fabsf(pc.ny * f01.y) + pc.omnz + pc.nz * eps;
     return D > 0.0f ? 3.0f * kCoordEps * mag / D : 0.0f;
 }
 
@@ -521,10 +560,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     const int B = p.block;
     const size_t sbytes = stage_bytes(B);
     constexpr int kWarpsMix = kMixThreads / 32;
-    // Slot numbering: the warp's jobs are ordered lane by lane (a lane's PIX pixels in
-    // turn), so the job offsets s_kp are indexed lane-major, wslot + lane * PIX + q; the
-    // per-slot data are indexed q-major, wslot + q * 32 + lane, so that a warp's accesses
-    // to its own slots are contiguous.
+    // Slot numbering: lane-major, wslot + lane * PIX + q for pixel q of a lane -- the
+    // order in which the warp's jobs are listed, so that the 32 jobs of a round, which
+    // mostly belong to consecutive slots, read consecutive per-slot records.
     __shared__ float4 s_wh[kSlots];                   // slope hi parts (w_x, w_y, w_z), row
     __shared__ int4 s_job[kSlots];                    // block: I, f, x_end
     __shared__ int s_ja[kSlots];                      // block: first grid point
@@ -563,7 +601,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         const DF wx = split_double(-nx * sc), wy = split_double(-ny * sc);
         const DF wz = split_double(omnz * sc);
         // .w: the pixel's row in the tile (bits of an unsigned), for the record address
-        s_wh[wslot + q * 32 + lane] =
+        s_wh[wslot + lane * PIX + q] =
             make_float4(wx.hi, wy.hi, wz.hi, __uint_as_float(q * kMixThreads + threadIdx.x));
         wlo[q][0] = wx.lo;
         wlo[q][1] = wy.lo;
@@ -707,7 +745,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 for (int c = 0; c < 8; ++c) an0[c] = __shfl_sync(0xffffffffu, anc32[c], 0);
 #pragma unroll
                 for (int q = 0; q < PIX; ++q) {   // block 0's anchor is sample 0
-                    anchor_of(an0, s_wh[wslot + q * 32 + lane], q, Is[q], fs[q]);
+                    anchor_of(an0, s_wh[wslot + lane * PIX + q], q, Is[q], fs[q]);
                     const int fl = frac_floor(fs[q]);
                     const float fr = fs[q] - (float)fl;
                     jdone[q] = Is[q] + fl;
@@ -729,7 +767,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             int tot = 0;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
-                const int sl = wslot + q * 32 + lane;
+                const int sl = wslot + lane * PIX + q;
                 const float4 wh = s_wh[sl];
                 int Ie = 0, jend;
                 float fe = 0.0f, xe;
@@ -835,16 +873,17 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 pc.ny = -w.y * inv_sc;
                 pc.omnz = w.z * inv_sc;
                 pc.nz = 1.0f - pc.omnz;
-                float Fb[3], Fa[3];
-                field_fp32<FL>(pc, s_field2 + 3 * a, c0_over_R, Fb);
-                field_fp32<FL>(pc, s_field2 + 3 * hb, c0_over_R, Fa);
                 const float du = __fsub_rn(xb, xa);
                 const float wb = du > 0.0f ? __fdividef(__fsub_rn(tJ, xa), du) : 0.0f;
                 const float wa = 1.0f - wb;
-                const float v0 = fmaf(Fb[0], wa, Fa[0] * wb), v1 = fmaf(Fb[1], wa, Fa[1] * wb);
-                const float v2 = fmaf(Fb[2], wa, Fa[2] * wb);
                 if (CHECK) {   // error estimate instead of the deposit
                     if (!(du > 0.0f)) return;
+                    float Fb[3], Fa[3];
+                    field_fp32<FL>(pc, s_field2 + 3 * a, c0_over_R, Fb);
+                    field_fp32<FL>(pc, s_field2 + 3 * hb, c0_over_R, Fa);
+                    const float v0 = fmaf(Fb[0], wa, Fa[0] * wb);
+                    const float v1 = fmaf(Fb[1], wa, Fa[1] * wb);
+                    const float v2 = fmaf(Fb[2], wa, Fa[2] * wb);
                     // the weight's: the field's change times the weight's rounding, from the
                     // sizes of the terms the two coordinates sum (the anchor's is exact, the
                     // next anchor's a double-FP32 difference)
@@ -866,8 +905,17 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     const float u0 = v0 * 0x1p-50f, u1 = v1 * 0x1p-50f, u2 = v2 * 0x1p-50f;
                     val2 = fmaf(u0, u0, fmaf(u1, u1, fmaf(u2, u2, val2)));
                 } else {
+                    // wa F(a) + wb F(hb), both ends in the expanded form
+                    const float2 nxy = make_float2(pc.nx, pc.ny);
+                    float2 tb, ta;
+                    float tbz, taz, sb, sa;
+                    end_terms<FL>(pc, nxy, s_field2 + 3 * a, c0_over_R, wa, tb, tbz, sb);
+                    end_terms<FL>(pc, nxy, s_field2 + 3 * hb, c0_over_R, wb, ta, taz, sa);
+                    const float2 vxy =
+                        __ffma2_rn(tb, make_float2(sb, sb), __fmul2_rn(ta, make_float2(sa, sa)));
+                    const float vz = fmaf(tbz, sb, taz * sa);
                     deposit3_row<ACC>(tile_rec + (uint64_t)__float_as_uint(w.w) * row_bytes, j,
-                                      p.n_bins, v0, v1, v2);
+                                      p.n_bins, vxy.x, vxy.y, vz);
                 }
             };
             // the warp's grid points: prefix sum of the runs over the warp's slots, and the
@@ -882,25 +930,20 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             int run = incl - tot;
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
-                s_kp[wslot + lane * PIX + q] = run;
-                const int sl = wslot + q * 32 + lane;
+                const int sl = wslot + lane * PIX + q;
+                s_kp[sl] = run;
                 for (int t = 0; t < K[q] && run + t < kJobTable; ++t)
                     s_tab[warp][run + t] = make_int2(sl, JA[q] + t);
                 run += K[q];
             }
             __syncwarp();
-            // slot (q-major) of the warp's job t beyond the table: the last slot whose
-            // offset is <= t (a lane-major search)
+            // slot of the warp's job t beyond the table: the last slot whose offset is <= t
             auto slot_of = [&](int t) -> int {
                 int pos = 0;
 #pragma unroll
                 for (int step = 16 * PIX; step > 0; step >>= 1)
                     if (s_kp[wslot + pos + step] <= t) pos += step;
-                return wslot + (pos % PIX) * 32 + pos / PIX;
-            };
-            auto slot_offset = [&](int sl) -> int {   // s_kp entry of q-major slot sl
-                const int r = sl - wslot;
-                return s_kp[wslot + (r % 32) * PIX + r / 32];
+                return wslot + pos;
             };
             for (int t = lane; t < T; t += 32) {
                 if (t < kJobTable) {
@@ -908,12 +951,12 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     job(e.x, e.y);
                 } else {
                     const int sl = slot_of(t);
-                    job(sl, s_ja[sl] + (t - slot_offset(sl)));
+                    job(sl, s_ja[sl] + (t - s_kp[sl]));
                 }
             }
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {   // runs too long for the warp's job count
-                const int sl = wslot + q * 32 + lane;
+                const int sl = wslot + lane * PIX + q;
                 for (int t = 0; t < big[q]; ++t) job(sl, JA[q] + t);
             }
             __syncwarp();   // s_job / s_kp are rewritten for the next block

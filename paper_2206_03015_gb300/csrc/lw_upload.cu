@@ -6,7 +6,7 @@
 //   MIXED  per sample a float4 (tau - tau_b, x - x_b, y - y_b, z - z_b) with the
 //          light-front time tau = t - z/c0 taken relative to the first sample of
 //          the sample's anchoring block, six floats of field data
-//          (beta_x, beta_y, 1 - beta_z, beta_dot), and per block the anchor
+//          (beta_x, beta_y, beta_dot_x, beta_dot_y, 1 - beta_z, beta_dot_z), and per block the anchor
 //          (tau_b in FP64, x_b, y_b, z_b as FP32 pairs).  Subtracting the anchor in FP64 keeps the FP32
 //          numbers small, so the FP32 part of the bin coordinate stays accurate.
 // lw_grid_bounds evaluates Eqs. (tu_min) and (tu_max).
@@ -153,11 +153,13 @@ __global__ void __launch_bounds__(kPrepThreads)
                 const double taub = s_taub[(i >> block_shift) - b_first];
                 scan[s] = make_float4(to_float(tau - taub), to_float(x - xb), to_float(y - yb),
                                       to_float(z - zb));
+                // (beta_x, beta_y), (beta_dot_x, beta_dot_y), (1 - beta_z, beta_dot_z): the
+                // x and y pairs are the operands of the deposit's packed FP32x2 arithmetic
                 s_out[6 * l] = b0f;
                 s_out[6 * l + 1] = b1f;
-                s_out[6 * l + 2] = epsf;
-                s_out[6 * l + 3] = to_float(a0);
-                s_out[6 * l + 4] = to_float(a1);
+                s_out[6 * l + 2] = to_float(a0);
+                s_out[6 * l + 3] = to_float(a1);
+                s_out[6 * l + 4] = epsf;
                 s_out[6 * l + 5] = to_float(a2);
                 if (i == ib) {   // position as FP32 pairs: hi = fl32(x), lo = fl32(x - hi)
                     Anchor an;

@@ -243,8 +243,9 @@ def test_mixed_section_values(block):
     assert np.all(np.abs(scan[..., 0] - dtau) <= 4e-16 * np.abs(tau) + 1e-7 * np.abs(dtau))
     assert np.array_equal(field[..., 0], tr.beta[..., 0].astype(np.float32))
     assert np.array_equal(field[..., 1], tr.beta[..., 1].astype(np.float32))
-    assert np.array_equal(field[..., 2], (1.0 - tr.beta[..., 2]).astype(np.float32))
-    assert np.array_equal(field[..., 3:], tr.beta_dot.astype(np.float32))
+    assert np.array_equal(field[..., 2:4], tr.beta_dot[..., :2].astype(np.float32))
+    assert np.array_equal(field[..., 4], (1.0 - tr.beta[..., 2]).astype(np.float32))
+    assert np.array_equal(field[..., 5], tr.beta_dot[..., 2].astype(np.float32))
 
 
 def test_config3_mixed_spectrum_per_band():
