@@ -82,51 +82,89 @@ __device__ __forceinline__ bool finite_bits(double v) {
 }
 
 
+// Blocks (of at least 16 samples) that one chunk of kPrepThreads samples can meet.
+constexpr int kChunkBlocks = kPrepThreads / 16 + 1;
+
 __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
                    int ns1, int block_shift, int n_blocks, float4* __restrict__ scan,
                    float* __restrict__ field, Anchor* __restrict__ anchor, int check_steps,
                    int32_t* __restrict__ status) {
-    __shared__ double s_in[3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
-    __shared__ float s_out[6 * kPrepThreads];       // field records of the chunk
-    __shared__ double s_taub[kPrepThreads];         // tau of the chunk's block starts
+    // two buffers: the next electron's chunk is copied in (cp.async) while this one is
+    // converted, so the loads of one chunk overlap the arithmetic and stores of the other
+    __shared__ double s_in[2][3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
+    __shared__ double s_t[2][kPrepThreads];           // its times (per-electron time axes)
+    __shared__ double s_blk[2][4][kChunkBlocks];      // (t, x, y, z) of its block starts
+    __shared__ double s_taub[2][kChunkBlocks];        // their light-front times
+    __shared__ __align__(16) float s_out[6 * kPrepThreads];   // field records of the chunk
     int bits = 0;
     const int i_first = blockIdx.x * kPrepThreads;
     const int cnt = min(kPrepThreads, ns1 - i_first);
     const int b_first = i_first >> block_shift;
     const int n_b = ((i_first + cnt - 1) >> block_shift) - b_first + 1;   // blocks met
-    for (int64_t k = blockIdx.y; k < n_e; k += gridDim.y) {
+    const int l = threadIdx.x;
+    const int i = i_first + l;
+    // a shared time axis is the same for every electron
+    const double t_shared = (!t_per_e && l < cnt) ? t[i] : 0.0;
+    auto prefetch = [&](int64_t k, int buf) {
         const int64_t s0 = k * ns1 + i_first;
-        __syncthreads();
-        for (int q = threadIdx.x; q < 3 * cnt; q += kPrepThreads) {
-            s_in[0][q] = r[3 * s0 + q];
-            s_in[1][q] = beta[3 * s0 + q];
-            s_in[2][q] = bdot[3 * s0 + q];
+        for (int q = l; q < 3 * cnt; q += kPrepThreads) {
+            cp_async8(&s_in[buf][0][q], r + 3 * s0 + q);
+            cp_async8(&s_in[buf][1][q], beta + 3 * s0 + q);
+            cp_async8(&s_in[buf][2][q], bdot + 3 * s0 + q);
         }
-        const double* tk = t + (t_per_e ? k * ns1 : 0);
-        if (scan && threadIdx.x < n_b) {   // once per block, not per sample (FP64 pipe)
-            const int ib = (b_first + threadIdx.x) << block_shift;
-            s_taub[threadIdx.x] = tk[ib] - r[3 * (k * ns1 + ib) + 2] * kInvC0;
+        if (t_per_e && l < cnt) cp_async8(&s_t[buf][l], t + s0 + l);
+        if (scan && l < n_b) {
+            const int64_t sb = k * ns1 + ((int64_t)(b_first + l) << block_shift);
+            cp_async8(&s_blk[buf][0][l], t + (t_per_e ? sb : sb - k * ns1));
+            for (int c = 0; c < 3; ++c) cp_async8(&s_blk[buf][1 + c][l], r + 3 * sb + c);
         }
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (blockIdx.y < n_e) prefetch(blockIdx.y, 0);
+    for (int64_t k = blockIdx.y; k < n_e; k += gridDim.y, buf ^= 1) {
+        const int64_t s0 = k * ns1 + i_first;
+        const int64_t kn = k + gridDim.y;
+        // the other buffer was released by the previous iteration's last barrier
+        if (kn < n_e) {
+            prefetch(kn, buf ^ 1);
+            cp_async_wait_one();   // this chunk's group is complete, the next may be in flight
+        } else {
+            cp_async_wait_all();
+        }
+        // a block start's light-front time, by the thread that copied it (its own copies
+        // are complete), once per block
+        if (scan && l < n_b) s_taub[buf][l] = s_blk[buf][0][l] - s_blk[buf][3][l] * kInvC0;
         __syncthreads();
         const bool check_t = t_per_e || k == 0;
-        const int l = threadIdx.x;
         if (l < cnt) {
-            const int i = i_first + l;
             const int64_t s = s0 + l;
-            const double x = s_in[0][3 * l], y = s_in[0][3 * l + 1], z = s_in[0][3 * l + 2];
-            const double b0 = s_in[1][3 * l], b1 = s_in[1][3 * l + 1], b2 = s_in[1][3 * l + 2];
-            const double a0 = s_in[2][3 * l], a1 = s_in[2][3 * l + 1], a2 = s_in[2][3 * l + 2];
-            const double ti = tk[i];
+            // the staged values are read as (lo, hi) integer words: those that are only
+            // checked and rounded to FP32 never become FP64 registers (which costs FP64-pipe
+            // instructions, the pass's bound); FP64 values are formed where FP64 arithmetic
+            // needs them
+            const double* in0 = s_in[buf][0];
+            const uint2* u1 = reinterpret_cast<const uint2*>(s_in[buf][1]);
+            const uint2* u2 = reinterpret_cast<const uint2*>(s_in[buf][2]);
+            const uint2* u0 = reinterpret_cast<const uint2*>(in0);
+            const uint2 xu = u0[3 * l], yu = u0[3 * l + 1], zu = u0[3 * l + 2];
+            const double x = __hiloint2double((int)xu.y, (int)xu.x);
+            const double y = __hiloint2double((int)yu.y, (int)yu.x);
+            const double z = __hiloint2double((int)zu.y, (int)zu.x);
+            const uint2 b0u = u1[3 * l], b1u = u1[3 * l + 1], b2u = u1[3 * l + 2];
+            const uint2 a0u = u2[3 * l], a1u = u2[3 * l + 1], a2u = u2[3 * l + 2];
+            const double b2 = __hiloint2double((int)b2u.y, (int)b2u.x);
+            const double ti = t_per_e ? s_t[buf][l] : t_shared;
+            auto fu = [](uint2 v) { return ((v.y >> 20) & 0x7ffu) != 0x7ffu; };   // isfinite
             const bool fin = finite_bits(x) & finite_bits(y) & finite_bits(z) &
-                             finite_bits(b0) & finite_bits(b1) & finite_bits(b2) &
-                             finite_bits(a0) & finite_bits(a1) & finite_bits(a2) &
+                             fu(b0u) & fu(b1u) & fu(b2u) & fu(a0u) & fu(a1u) & fu(a2u) &
                              finite_bits(ti);
             if (!fin) bits |= LW_ST_NONFINITE;
             // |beta| < 1: decided in FP32 when 1 - beta^2 is far above its FP32 rounding,
             // else by the FP64 expression ((bx*bx + by*by) + bz*bz) < 1
-            const float b0f = to_float(b0), b1f = to_float(b1);
+            const float b0f = to_float_bits(b0u.y, b0u.x), b1f = to_float_bits(b1u.y, b1u.x);
             const float epsf = to_float(1.0 - b2);   // exact in FP64 for b2 in [0.5, 2]
             const float perp = fmaf(b0f, b0f, b1f * b1f);
             const float one_minus = fmaf(-epsf, epsf, 2.0f * epsf) - perp;   // 1 - beta^2
@@ -134,33 +172,37 @@ __global__ void __launch_bounds__(kPrepThreads)
             // FP64 test and fails it)
             const bool b2_half = __double2hiint(b2) >= 0x3fe00000;
             if (!(b2_half && one_minus > 1.0e-5f * (2.0f * epsf + perp))) {
+                const double b0 = __hiloint2double((int)b0u.y, (int)b0u.x);
+                const double b1 = __hiloint2double((int)b1u.y, (int)b1u.x);
                 const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)),
                                             __dmul_rn(b2, b2));
                 if (!(bb < 1.0)) bits |= LW_ST_BETA;
             }
+            const double* tk = t + (t_per_e ? k * ns1 : 0);
             if (check_t && i > 0 && !(ti > tk[i - 1])) bits |= LW_ST_TIME;
             if (check_steps && i > 0) {   // |r_i - r_(i-1)| < c0 (t_i - t_(i-1)), in FP64
-                const double* pr = l > 0 ? &s_in[0][3 * (l - 1)] : r + 3 * (s - 1);
+                const double* pr = l > 0 ? &in0[3 * (l - 1)] : r + 3 * (s - 1);
                 const double dx = x - pr[0], dy = y - pr[1], dz = z - pr[2];
                 const double ct = kC0 * (ti - tk[i - 1]);
                 if (!(dx * dx + dy * dy + dz * dz < ct * ct)) bits |= LW_ST_STEP;
             }
             if (scan) {
                 const int ib = (i >> block_shift) << block_shift;
-                const int64_t sb = k * ns1 + ib;
-                const double xb = r[3 * sb], yb = r[3 * sb + 1], zb = r[3 * sb + 2];
+                const int jb = (i >> block_shift) - b_first;
+                const double xb = s_blk[buf][1][jb], yb = s_blk[buf][2][jb],
+                             zb = s_blk[buf][3][jb];
                 const double tau = ti - z * kInvC0;
-                const double taub = s_taub[(i >> block_shift) - b_first];
+                const double taub = s_taub[buf][jb];
                 scan[s] = make_float4(to_float(tau - taub), to_float(x - xb), to_float(y - yb),
                                       to_float(z - zb));
                 // (beta_x, beta_y), (beta_dot_x, beta_dot_y), (1 - beta_z, beta_dot_z): the
                 // x and y pairs are the operands of the deposit's packed FP32x2 arithmetic
                 s_out[6 * l] = b0f;
                 s_out[6 * l + 1] = b1f;
-                s_out[6 * l + 2] = to_float(a0);
-                s_out[6 * l + 3] = to_float(a1);
+                s_out[6 * l + 2] = to_float_bits(a0u.y, a0u.x);
+                s_out[6 * l + 3] = to_float_bits(a1u.y, a1u.x);
                 s_out[6 * l + 4] = epsf;
-                s_out[6 * l + 5] = to_float(a2);
+                s_out[6 * l + 5] = to_float_bits(a2u.y, a2u.x);
                 if (i == ib) {   // position as FP32 pairs: hi = fl32(x), lo = fl32(x - hi)
                     Anchor an;
                     an.tau = taub;
@@ -176,8 +218,19 @@ __global__ void __launch_bounds__(kPrepThreads)
         }
         if (scan) {
             __syncthreads();
-            for (int q = threadIdx.x; q < 6 * cnt; q += kPrepThreads) field[6 * s0 + q] = s_out[q];
+            // 24 bytes per sample: 16-byte stores when the chunk starts on a 16-byte boundary
+            float* dst = field + 6 * s0;
+            if (((uintptr_t)dst & 15u) == 0) {
+                const int n4 = (6 * cnt) >> 2;
+                for (int q = l; q < n4; q += kPrepThreads)
+                    reinterpret_cast<float4*>(dst)[q] = reinterpret_cast<const float4*>(s_out)[q];
+                for (int q = 4 * n4 + l; q < 6 * cnt; q += kPrepThreads) dst[q] = s_out[q];
+            } else {   // 8-byte aligned: 24 s0 bytes past an aligned section
+                for (int q = l; q < 3 * cnt; q += kPrepThreads)
+                    reinterpret_cast<float2*>(dst)[q] = reinterpret_cast<const float2*>(s_out)[q];
+            }
         }
+        __syncthreads();   // both buffers are free for the next prefetch
     }
     block_status_or(status, bits);
 }
