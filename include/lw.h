@@ -143,8 +143,9 @@ typedef struct {
     const double* beta_dot;
     const void* scan;       /* MIXED: float4 [n_e][n_s+1] (tau - tau_b, r - r_b) per sample,
                                tau = t - z/c0, _b = first sample of the sample's block */
-    const void* field;      /* MIXED: float [n_e][n_s+1][6] (beta_x, beta_y, beta_dot_x,
-                               beta_dot_y, 1 - beta_z, beta_dot_z) */
+    const void* field;      /* MIXED: float4 [n_e][n_s+1] (beta_x, beta_y, beta_dot_x,
+                               beta_dot_y), then float2 [n_e][n_s+1] (1 - beta_z,
+                               beta_dot_z) */
     const double* anchor;   /* MIXED: 32-byte records [n_e][n_blocks]: tau_b (double), then
                                x_b, y_b, z_b as float pairs (hi, lo), hi = fl32(x),
                                lo = fl32(x - hi) */

@@ -45,7 +45,8 @@ struct DepositArgs {
     const double* beta;
     const double* bdot;
     const float4* scan;
-    const float* field;
+    const float4* field4;    // (beta_x, beta_y, beta_dot_x, beta_dot_y) per sample
+    const float2* field2;    // (1 - beta_z, beta_dot_z) per sample
     const Anchor* anchor;
     int block, n_blocks;
     const int32_t* input_status;
@@ -277,14 +278,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Per-sample FP32 field in the stable form, for the field terms FL (LW_FIELD_* mask, a
 // compile-time constant); zero if D <= 0.
-// f: the sample's six field floats as three 8-byte-aligned pairs
-// (beta_x, beta_y), (beta_dot_x, beta_dot_y), (1 - beta_z, beta_dot_z).
+// f4 = (beta_x, beta_y, beta_dot_x, beta_dot_y), f2 = (1 - beta_z, beta_dot_z).
 template <int FL>
-__device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* __restrict__ f,
+__device__ __forceinline__ void field_fp32(const PixelConst& pc, float4 f4, float2 f2,
                                            float c0_over_R, float F[3]) {
-    const float2 f01 = f[0], f23 = f[1], f45 = f[2];
-    const float bx = f01.x, by = f01.y, eps = f45.x;
-    const float ax = f23.x, ay = f23.y, az = f45.y;
+    const float bx = f4.x, by = f4.y, eps = f2.x;
+    const float ax = f4.z, ay = f4.w, az = f2.y;
     const float D = fmaf(-pc.ny, by, fmaf(-pc.nx, bx, fmaf(pc.nz, eps, pc.omnz)));
     const float mx = pc.nx - bx, my = pc.ny - by, mz = eps - pc.omnz;
     const float invD = rcp_approx(D);
@@ -315,10 +314,10 @@ __device__ __forceinline__ void field_fp32(const PixelConst& pc, const float2* _
 // k m - beta_dot (x and y packed for the FP32x2 instructions, z) and the scale
 // weight / D^2 (zero if D <= 0), so that the interpolated value is t_a s_a + t_b s_b.
 template <int FL>
-__device__ __forceinline__ void end_terms(const PixelConst& pc, float2 nxy,
-                                          const float2* __restrict__ f, float c0_over_R,
-                                          float weight, float2& txy, float& tz, float& sc) {
-    const float2 b = f[0], a = f[1], ez = f[2];   // (bx, by), (ax, ay), (1 - bz, az)
+__device__ __forceinline__ void end_terms(const PixelConst& pc, float2 nxy, float4 f4, float2 ez,
+                                          float c0_over_R, float weight, float2& txy,
+                                          float& tz, float& sc) {
+    const float2 b = make_float2(f4.x, f4.y), a = make_float2(f4.z, f4.w);   // beta, beta_dot
     const float D = fmaf(-pc.ny, b.y, fmaf(-pc.nx, b.x, fmaf(pc.nz, ez.x, pc.omnz)));
     const float2 m = __ffma2_rn(b, make_float2(-1.0f, -1.0f), nxy);
     const float mz = ez.x - pc.omnz;
@@ -426,17 +425,21 @@ __device__ __forceinline__ float coord(float4 w, float s, float4 sc) {
 // completion counted in bytes on one mbarrier per buffer), kMixStages - 1 blocks ahead
 // of the block being processed.  One buffer holds block b's samples i0 .. i0+B-1 as
 // float4 (block-relative light-front time and position), the field records of samples
-// i0 .. i0+B (the next block's first sample included) and, with block 0 and with every
-// block b of b % 32 == 31, the FP64 anchors of the next 32 blocks.
+// i0 .. i0+B (the next block's first sample included) as a float4 array and a float2
+// array and, with block 0 and with every block b of b % 32 == 31, the FP64 anchors of the
+// next 32 blocks.
 #ifndef LW_MIX_STAGES
 #define LW_MIX_STAGES 2
 #endif
 constexpr int kMixStages = LW_MIX_STAGES;
 constexpr int kAnchorBatch = 32;
-__host__ __device__ constexpr size_t stage_field_off(int B) { return 16 * (size_t)B; }
+__host__ __device__ constexpr size_t stage_f4_off(int B) { return 16 * (size_t)B; }
+__host__ __device__ constexpr size_t stage_f2_off(int B) {
+    return stage_f4_off(B) + 16 * ((size_t)B + 1);
+}
 __host__ __device__ constexpr size_t stage_anchor_off(int B) {
-    // field records: 24 (B + 1) bytes copied from a 16-byte aligned start up to 8 bytes early
-    return (stage_field_off(B) + 24 * ((size_t)B + 1) + 8 + 15 + 31) / 32 * 32;
+    // float2 records: 8 (B + 1) bytes copied from a 16-byte aligned start up to 8 bytes early
+    return (stage_f2_off(B) + 8 * ((size_t)B + 1) + 8 + 15 + 31) / 32 * 32;
 }
 __host__ __device__ constexpr size_t stage_bytes(int B) {
     return stage_anchor_off(B) + sizeof(Anchor) * kAnchorBatch;
@@ -522,9 +525,9 @@ __device__ __forceinline__ float coord_mag(float4 w, float s, float4 sc) {
 // Relative error of an FP32 field through its Doppler factor: D sums terms of size
 // (1 - n_z) + n_z (1 - beta_z) + |n_x beta_x| + |n_y beta_y|, each rounded to about an ulp,
 // and enters the field as D^-3.
-__device__ __forceinline__ float fd_rel(const PixelConst& pc, const float2* __restrict__ f) {
-    const float2 f01 = f[0];
-    const float eps = f[2].x;
+__device__ __forceinline__ float fd_rel(const PixelConst& pc, float4 f4, float2 f2) {
+    const float2 f01 = make_float2(f4.x, f4.y);
+    const float eps = f2.x;
     const float D = fmaf(-pc.ny, f01.y, fmaf(-pc.nx, f01.x, fmaf(pc.nz, eps, pc.omnz)));
     const float mag = fabsf(pc.nx * f01.x) + fabsf(pc.ny * f01.y) + pc.omnz + pc.nz * eps;
     return D > 0.0f ? 3.0f * kCoordEps * mag / D : 0.0f;
@@ -620,8 +623,8 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     auto electron = [&](int64_t kk) -> int64_t { return p.order ? (int64_t)p.order[kk] : kk; };
     // blocks with at least one step: ceil((ns1 - 1) / B)
     const int nbs = (int)((p.ns1 - 2) / B + 1);
-    // field records of a block start 0 or 8 bytes into the buffer's field area: the
-    // bulk copy starts at the 16-byte boundary at or before the block's first record
+    // float2 field records of a block start 0 or 8 bytes into their area: the bulk copy
+    // starts at the 16-byte boundary at or before the block's first record
     auto field_shift = [&](int64_t k, int b) -> int {
         return (int)((k * p.ns1 + (int64_t)b * B) & 1) * 8;
     };
@@ -632,16 +635,18 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         const int ns = (int)min((int64_t)B, p.ns1 - 1 - i0);   // steps of the block
         const unsigned scan_bytes = 16u * (unsigned)min((int64_t)B, p.ns1 - i0);
         const int sh = field_shift(k, b);
-        const unsigned field_bytes = (24u * (unsigned)(ns + 1) + (unsigned)sh + 15u) & ~15u;
+        const unsigned f4_bytes = 16u * (unsigned)(ns + 1);
+        const unsigned f2_bytes = (8u * (unsigned)(ns + 1) + (unsigned)sh + 15u) & ~15u;
         const int a0 = b == 0 ? 0 : ((b & (kAnchorBatch - 1)) == kAnchorBatch - 1 ? b + 1 : -1);
         const unsigned anc_bytes =
             a0 >= 0 ? (unsigned)(sizeof(Anchor) * min(kAnchorBatch, p.n_blocks - a0)) : 0u;
         fence_proxy_async_smem();   // the buffer's previous contents were read by the CTA
-        mbar_expect_tx(&s_full[buf], scan_bytes + field_bytes + anc_bytes);
+        mbar_expect_tx(&s_full[buf], scan_bytes + f4_bytes + f2_bytes + anc_bytes);
         bulk_g2s(base, p.scan + k * p.ns1 + i0, scan_bytes, &s_full[buf]);
-        bulk_g2s(base + stage_field_off(B),
-                 reinterpret_cast<const unsigned char*>(p.field + 6 * (k * p.ns1 + i0)) - sh,
-                 field_bytes, &s_full[buf]);
+        bulk_g2s(base + stage_f4_off(B), p.field4 + k * p.ns1 + i0, f4_bytes, &s_full[buf]);
+        bulk_g2s(base + stage_f2_off(B),
+                 reinterpret_cast<const unsigned char*>(p.field2 + k * p.ns1 + i0) - sh,
+                 f2_bytes, &s_full[buf]);
         if (anc_bytes)
             bulk_g2s(base + stage_anchor_off(B), p.anchor + k * p.n_blocks + a0, anc_bytes,
                      &s_full[buf]);
@@ -731,8 +736,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
             issue_next(cur == 0 ? kMixStages - 1 : cur - 1);
             const unsigned char* base = smem_raw + cur * sbytes;
             const float4* s_scan = reinterpret_cast<const float4*>(base);
-            const float2* s_field2 =
-                reinterpret_cast<const float2*>(base + stage_field_off(B) + field_shift(k, b));
+            const float4* s_f4 = reinterpret_cast<const float4*>(base + stage_f4_off(B));
+            const float2* s_f2 =
+                reinterpret_cast<const float2*>(base + stage_f2_off(B) + field_shift(k, b));
             const Anchor* s_anc = reinterpret_cast<const Anchor*>(base + stage_anchor_off(B));
             cur = cur + 1 == kMixStages ? 0 : cur + 1;
             // anchors: lane l holds the FP32 pairs of anchor 32c + l (c = batch); block b's
@@ -879,8 +885,8 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 if (CHECK) {   // error estimate instead of the deposit
                     if (!(du > 0.0f)) return;
                     float Fb[3], Fa[3];
-                    field_fp32<FL>(pc, s_field2 + 3 * a, c0_over_R, Fb);
-                    field_fp32<FL>(pc, s_field2 + 3 * hb, c0_over_R, Fa);
+                    field_fp32<FL>(pc, s_f4[a], s_f2[a], c0_over_R, Fb);
+                    field_fp32<FL>(pc, s_f4[hb], s_f2[hb], c0_over_R, Fa);
                     const float v0 = fmaf(Fb[0], wa, Fa[0] * wb);
                     const float v1 = fmaf(Fb[1], wa, Fa[1] * wb);
                     const float v2 = fmaf(Fb[2], wa, Fa[2] * wb);
@@ -894,9 +900,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     float e = dw * (fabsf(Fa[0] - Fb[0]) + fabsf(Fa[1] - Fb[1]) +
                                     fabsf(Fa[2] - Fb[2]));
                     // the fields': D in FP32 loses the terms' size over D, three times in D^3
-                    e = fmaf(fd_rel(pc, s_field2 + 3 * a) * wa,
+                    e = fmaf(fd_rel(pc, s_f4[a], s_f2[a]) * wa,
                              fabsf(Fb[0]) + fabsf(Fb[1]) + fabsf(Fb[2]), e);
-                    e = fmaf(fd_rel(pc, s_field2 + 3 * hb) * wb,
+                    e = fmaf(fd_rel(pc, s_f4[hb], s_f2[hb]) * wb,
                              fabsf(Fa[0]) + fabsf(Fa[1]) + fabsf(Fa[2]), e);
                     // squares of the values scaled by 2^-100 (fields of up to ~1e35 /s stay in
                     // range)
@@ -909,8 +915,8 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                     const float2 nxy = make_float2(pc.nx, pc.ny);
                     float2 tb, ta;
                     float tbz, taz, sb, sa;
-                    end_terms<FL>(pc, nxy, s_field2 + 3 * a, c0_over_R, wa, tb, tbz, sb);
-                    end_terms<FL>(pc, nxy, s_field2 + 3 * hb, c0_over_R, wb, ta, taz, sa);
+                    end_terms<FL>(pc, nxy, s_f4[a], s_f2[a], c0_over_R, wa, tb, tbz, sb);
+                    end_terms<FL>(pc, nxy, s_f4[hb], s_f2[hb], c0_over_R, wb, ta, taz, sa);
                     const float2 vxy =
                         __ffma2_rn(tb, make_float2(sb, sb), __fmul2_rn(ta, make_float2(sa, sa)));
                     const float vz = fmaf(tbz, sb, taz * sa);
@@ -1386,7 +1392,10 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
     a.beta = traj->beta;
     a.bdot = traj->beta_dot;
     a.scan = static_cast<const float4*>(traj->scan);
-    a.field = static_cast<const float*>(traj->field);
+    a.field4 = static_cast<const float4*>(traj->field);
+    a.field2 = traj->field
+                   ? reinterpret_cast<const float2*>(a.field4 + traj->n_e * (traj->n_s + 1))
+                   : nullptr;
     a.anchor = reinterpret_cast<const Anchor*>(traj->anchor);
     a.block = traj->block;
     a.n_blocks = traj->n_blocks;
@@ -1506,7 +1515,10 @@ extern "C" int lw_batch_plan(const lw_batch_item* items, int32_t n_items, int32_
         a.ns1 = it.traj->n_s + 1;
         a.t_per_e = it.traj->t_per_electron;
         a.scan = static_cast<const float4*>(it.traj->scan);
-        a.field = static_cast<const float*>(it.traj->field);
+        a.field4 = static_cast<const float4*>(it.traj->field);
+        a.field2 = it.traj->field ? reinterpret_cast<const float2*>(
+                                        a.field4 + it.traj->n_e * (it.traj->n_s + 1))
+                                  : nullptr;
         a.anchor = reinterpret_cast<const Anchor*>(it.traj->anchor);
         a.block = it.traj->block;
         a.n_blocks = it.traj->n_blocks;

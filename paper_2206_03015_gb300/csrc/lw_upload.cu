@@ -89,15 +89,14 @@ __global__ void __launch_bounds__(kPrepThreads)
     prepare_kernel(const double* __restrict__ t, int t_per_e, const double* __restrict__ r,
                    const double* __restrict__ beta, const double* __restrict__ bdot, int64_t n_e,
                    int ns1, int block_shift, int n_blocks, float4* __restrict__ scan,
-                   float* __restrict__ field, Anchor* __restrict__ anchor, int check_steps,
-                   int32_t* __restrict__ status) {
+                   float4* __restrict__ field4, float2* __restrict__ field2,
+                   Anchor* __restrict__ anchor, int check_steps, int32_t* __restrict__ status) {
     // two buffers: the next electron's chunk is copied in (cp.async) while this one is
     // converted, so the loads of one chunk overlap the arithmetic and stores of the other
     __shared__ double s_in[2][3][3 * kPrepThreads];   // r, beta, beta_dot of the chunk
     __shared__ double s_t[2][kPrepThreads];           // its times (per-electron time axes)
     __shared__ double s_blk[2][4][kChunkBlocks];      // (t, x, y, z) of its block starts
     __shared__ double s_taub[2][kChunkBlocks];        // their light-front times
-    __shared__ __align__(16) float s_out[6 * kPrepThreads];   // field records of the chunk
     int bits = 0;
     const int i_first = blockIdx.x * kPrepThreads;
     const int cnt = min(kPrepThreads, ns1 - i_first);
@@ -195,14 +194,12 @@ __global__ void __launch_bounds__(kPrepThreads)
                 const double taub = s_taub[buf][jb];
                 scan[s] = make_float4(to_float(tau - taub), to_float(x - xb), to_float(y - yb),
                                       to_float(z - zb));
-                // (beta_x, beta_y), (beta_dot_x, beta_dot_y), (1 - beta_z, beta_dot_z): the
-                // x and y pairs are the operands of the deposit's packed FP32x2 arithmetic
-                s_out[6 * l] = b0f;
-                s_out[6 * l + 1] = b1f;
-                s_out[6 * l + 2] = to_float_bits(a0u.y, a0u.x);
-                s_out[6 * l + 3] = to_float_bits(a1u.y, a1u.x);
-                s_out[6 * l + 4] = epsf;
-                s_out[6 * l + 5] = to_float_bits(a2u.y, a2u.x);
+                // (beta_x, beta_y, beta_dot_x, beta_dot_y) and (1 - beta_z, beta_dot_z): one
+                // 16-byte and one 8-byte record, each a single shared-memory load in the
+                // deposit; the x and y pairs are operands of its packed FP32x2 arithmetic
+                field4[s] = make_float4(b0f, b1f, to_float_bits(a0u.y, a0u.x),
+                                        to_float_bits(a1u.y, a1u.x));
+                field2[s] = make_float2(epsf, to_float_bits(a2u.y, a2u.x));
                 if (i == ib) {   // position as FP32 pairs: hi = fl32(x), lo = fl32(x - hi)
                     Anchor an;
                     an.tau = taub;
@@ -214,20 +211,6 @@ __global__ void __launch_bounds__(kPrepThreads)
                     an.z_lo = __double2float_rn(zb - (double)an.z_hi);
                     anchor[k * n_blocks + (i >> block_shift)] = an;
                 }
-            }
-        }
-        if (scan) {
-            __syncthreads();
-            // 24 bytes per sample: 16-byte stores when the chunk starts on a 16-byte boundary
-            float* dst = field + 6 * s0;
-            if (((uintptr_t)dst & 15u) == 0) {
-                const int n4 = (6 * cnt) >> 2;
-                for (int q = l; q < n4; q += kPrepThreads)
-                    reinterpret_cast<float4*>(dst)[q] = reinterpret_cast<const float4*>(s_out)[q];
-                for (int q = 4 * n4 + l; q < 6 * cnt; q += kPrepThreads) dst[q] = s_out[q];
-            } else {   // 8-byte aligned: 24 s0 bytes past an aligned section
-                for (int q = l; q < 3 * cnt; q += kPrepThreads)
-                    reinterpret_cast<float2*>(dst)[q] = reinterpret_cast<const float2*>(s_out)[q];
             }
         }
         __syncthreads();   // both buffers are free for the next prefetch
@@ -466,7 +449,11 @@ extern "C" int lw_trajectories_upload(const lw_traj_in* in, int32_t sections, in
     const dim3 g((unsigned)((ns1 + kPrepThreads - 1) / kPrepThreads),
                  (unsigned)std::min<int64_t>(in->n_e, 65535));
     prepare_kernel<<<g, kPrepThreads, 0, st>>>(t, t_per_e, r, beta, bdot, in->n_e, (int)ns1, shift,
-                                          L.n_blocks, scan, field, anchor,
+                                          L.n_blocks, scan, reinterpret_cast<float4*>(field),
+                                          field ? reinterpret_cast<float2*>(
+                                                      field + 4 * (size_t)(in->n_e * ns1))
+                                                : nullptr,
+                                          anchor,
                                           (sections & LW_SECTION_FP64) ? 1 : 0, status);
     if (launch_status() != LW_OK) return LW_ECUDA;
     {

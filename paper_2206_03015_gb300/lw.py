@@ -228,8 +228,10 @@ class Trajectories:
         return self.view.n_s
 
     def mixed_section(self):
-        """(scan [n_e, n_s+1, 4], field [n_e, n_s+1, 6]) float32 views of the mixed section
-        in the workspace, or None without it."""
+        """(scan [n_e, n_s+1, 4] view, field [n_e, n_s+1, 6] copy) float32 of the mixed section
+        in the workspace, or None without it.  The field's columns are (beta_x, beta_y,
+        beta_dot_x, beta_dot_y, 1 - beta_z, beta_dot_z), stored as a float4 array followed
+        by a float2 array."""
         if not self.view.scan:
             return None
         ns1 = self.n_s + 1
@@ -238,8 +240,9 @@ class Trajectories:
             off = ptr - self.ws.data_ptr()
             return self.ws[off:off + nbytes].view(torch.float32)
         scan = at(self.view.scan, 16 * self.n_e * ns1).view(self.n_e, ns1, 4)
-        field = at(self.view.field, 24 * self.n_e * ns1).view(self.n_e, ns1, 6)
-        return scan, field
+        f4 = at(self.view.field, 16 * self.n_e * ns1).view(self.n_e, ns1, 4)
+        f2 = at(self.view.field + 16 * self.n_e * ns1, 8 * self.n_e * ns1).view(self.n_e, ns1, 2)
+        return scan, torch.cat([f4, f2], dim=-1)
 
     def order(self):
         """The electron visiting order of the deposits (int32 [n_e] view into the
