@@ -717,9 +717,10 @@ def run_c5(args):
 def run_c4(args):
     """Config 4: gradient of the band-integrated spectral energy (+-5 % of the on-axis
     fundamental) with respect to every electron's initial momentum and the laser's a0 and
-    w0, through the library's kernels only (GPU Boris push, FP64 deposit and spectrum,
-    lw_spectrum_grad, forward-mode lw_boris_push_grad); each part timed with CUDA events.
-    Beside it, once, the same gradient with the torch-written checkpointed pusher."""
+    w0, through the library's kernels only: GPU Boris push, mixed-precision deposit and
+    spectrum (the loss is FP32), the mixed-precision lw_spectrum_grad and the forward-mode
+    lw_boris_push_grad; each part timed with CUDA events.  Beside it the same chain in
+    FP64 and, once, the FP64 gradient with the torch-written checkpointed pusher."""
     import torch
 
     from paper_2206_03015_gb300 import lw
@@ -736,6 +737,7 @@ def run_c4(args):
     r0 = torch.from_numpy(r0n).to(dev)
     L4 = (laser.lam, laser.a0, laser.w0, laser.fwhm)
     dt = (t1 - t0) / n_s
+    MIX = lw.LW_MIXED_F32X4
     # the grid from one forward push (Eqs. tu_min / tu_max)
     t = torch.empty(n_s + 1, dtype=torch.float64, device=dev)
     R, B, A = (torch.empty((n_e, n_s + 1, 3), dtype=torch.float64, device=dev) for _ in range(3))
@@ -751,53 +753,61 @@ def run_c4(args):
         e.record()
         return e
 
-    def grad_step():
+    def grad_step(prec):
         u = torch.from_numpy(u0n).to(dev).requires_grad_(True)
         a0 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
         w0 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
-        e0 = ev()
-        S = PushSpectrum.apply(u, a0, w0, r0, laser.lam, laser.fwhm, t0, t1, n_s, det, grid)
-        L = band_energy(S, grid, mask)
-        e1 = ev()
+        S = PushSpectrum.apply(u, a0, w0, r0, laser.lam, laser.fwhm, t0, t1, n_s, det, grid,
+                               lw.Q_E, prec)
+        L = band_energy(S.to(torch.float64), grid, mask)
         L.backward()
-        e2 = ev()
-        return L, u.grad, a0.grad, w0.grad, (e0, e1, e2)
+        return L, u.grad, a0.grad, w0.grad
 
-    for _ in range(args.warmup):
-        grad_step()
-    torch.cuda.synchronize()
-    fw, bw = [], []
-    s0 = ev()
-    for _ in range(args.steps):
-        L, gu, ga, gw, (e0, e1, e2) = grad_step()
-    s1 = ev()
-    torch.cuda.synchronize()
-    ms = s0.elapsed_time(s1) / args.steps
-    # the parts, once more, each bracketed by events
-    parts = {}
-    u0d = torch.from_numpy(u0n).to(dev)
-    t = torch.empty(n_s + 1, dtype=torch.float64, device=dev)
-    R, B, A = (torch.empty((n_e, n_s + 1, 3), dtype=torch.float64, device=dev) for _ in range(3))
-    marks = [ev()]
-    lw.lw_boris_push(r0.clone(), u0d.clone(), t0, dt, n_s, L4, t, R, B, A)
-    marks.append(ev())
-    traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_FP64, device=dev)
-    marks.append(ev())
-    rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
-    marks.append(ev())
-    S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, want_X=True)
-    marks.append(ev())
-    gS = (mask.to(dev) * (2.0 * math.pi / (grid.n_bins * grid.dt_u)))[None, :].expand_as(S)
-    g_r, g_b, g_a = lw.lw_spectrum_grad(traj, det, grid, X, gS.contiguous())
-    marks.append(ev())
-    lw.lw_boris_push_grad(r0, u0d, t0, dt, n_s, L4, g_r, g_b, g_a)
-    marks.append(ev())
-    torch.cuda.synchronize()
-    for name, a, b in zip(("push", "upload", "deposit_fp64", "spectrum_fp64", "spectrum_grad",
-                           "push_grad"), marks[:-1], marks[1:]):
-        parts[name] = a.elapsed_time(b)
-    del traj, rec, S, X, g_r, g_b, g_a, t, R, B, A
-    # the torch-written checkpointed pusher (autograd) with the library's deposit adjoint
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            grad_step(prec)
+        torch.cuda.synchronize()
+        s0 = ev()
+        for _ in range(steps):
+            L, gu, ga, gw = grad_step(prec)
+        s1 = ev()
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / steps, (L, gu, ga, gw)
+
+    ms, (L, gu, ga, gw) = timed(MIX, args.steps, args.warmup)
+    ms64, (L64, gu64, ga64, gw64) = timed(lw.LW_FP64, 1, 1)
+
+    def parts_of(prec):
+        # the parts, once more, each bracketed by events
+        u0d = torch.from_numpy(u0n).to(dev)
+        t = torch.empty(n_s + 1, dtype=torch.float64, device=dev)
+        R, B, A = (torch.empty((n_e, n_s + 1, 3), dtype=torch.float64, device=dev)
+                   for _ in range(3))
+        sec = lw.LW_SECTION_FP64 if prec == lw.LW_FP64 else \
+            lw.LW_SECTION_FP64 | lw.LW_SECTION_MIXED
+        marks = [ev()]
+        lw.lw_boris_push(r0.clone(), u0d.clone(), t0, dt, n_s, L4, t, R, B, A)
+        marks.append(ev())
+        traj = lw.lw_trajectories_upload(t, R, B, A, sections=sec, device=dev)
+        marks.append(ev())
+        rec = lw.lw_deposit_time_domain(traj, det, grid, prec)
+        marks.append(ev())
+        S, X = lw.lw_spectrum(rec, prec, det.n_pix, grid, want_X=True)
+        marks.append(ev())
+        gS = (mask.to(dev) * (2.0 * math.pi / (grid.n_bins * grid.dt_u)))[None, :].expand(
+            S.shape).to(torch.float64)
+        g_r, g_b, g_a = lw.lw_spectrum_grad(traj, det, grid, X, gS.contiguous(), precision=prec)
+        marks.append(ev())
+        lw.lw_boris_push_grad(r0, u0d, t0, dt, n_s, L4, g_r, g_b, g_a)
+        marks.append(ev())
+        torch.cuda.synchronize()
+        return {name: a.elapsed_time(b) for name, a, b in zip(
+            ("push", "upload", "deposit", "spectrum", "spectrum_grad", "push_grad"),
+            marks[:-1], marks[1:])}
+
+    parts = parts_of(MIX)
+    parts64 = parts_of(lw.LW_FP64)
+    # the torch-written checkpointed pusher (autograd) with the library's FP64 adjoint
     ref = None
     if not args.no_torch_pusher:
         u = torch.from_numpy(u0n).to(dev).requires_grad_(True)
@@ -812,23 +822,32 @@ def run_c4(args):
         e1 = ev()
         torch.cuda.synchronize()
         ref = {"ms": e0.elapsed_time(e1),
-               "grad_rel_diff_u0": float(torch.linalg.norm(u.grad - gu) / torch.linalg.norm(gu)),
-               "grad_rel_diff_a0": float(abs(a0.grad - ga) / abs(ga)),
-               "grad_rel_diff_w0": float(abs(w0.grad - gw) / abs(gw))}
+               "grad_rel_diff_u0": float(torch.linalg.norm(u.grad - gu64) /
+                                         torch.linalg.norm(gu64)),
+               "grad_rel_diff_a0": float(abs(a0.grad - ga64) / abs(ga64)),
+               "grad_rel_diff_w0": float(abs(w0.grad - gw64) / abs(gw64))}
     dep = n_e * n_s * det.n_pix
     return {"metric": METRIC, "value": dep / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"c4 gradient: {n_e} co-located electrons (gamma 60 +-0.1%) x "
                                    f"{n_s} Boris steps in a 1 um, a0 = 1, 10 fs, w0 = 20 um laser, "
                                    f"{int(round(det.n_pix ** 0.5))}^2 pixels over +-1/gamma, "
                                    f"{n_bins} bins; loss = spectral energy within +-5% of the "
                                    f"on-axis fundamental; gradient w.r.t. u0 (all electrons), a0, w0",
                        "deposits_per_step": dep,
-                       "step": "forward (push, upload, FP64 deposit, spectrum) + backward "
-                               "(lw_spectrum_grad, lw_boris_push_grad)"},
+                       "step": "forward (push, upload, mixed deposit, FP32 spectrum) + backward "
+                               "(mixed lw_spectrum_grad, lw_boris_push_grad)"},
             "parts_ms": parts, "loss": float(L), "grad_a0": float(ga), "grad_w0": float(gw),
+            "fp64_chain": {"ms_per_step": ms64, "parts_ms": parts64, "loss": float(L64),
+                           "grad_a0": float(ga64), "grad_w0": float(gw64),
+                           "mixed_vs_fp64": {
+                               "loss": abs(float(L) / float(L64) - 1.0),
+                               "grad_u0_rel_l2": float(torch.linalg.norm(gu - gu64) /
+                                                       torch.linalg.norm(gu64)),
+                               "grad_a0": float(abs(ga - ga64) / abs(ga64)),
+                               "grad_w0": float(abs(gw - gw64) / abs(gw64))}},
             "torch_pusher": ref}
 
 

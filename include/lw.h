@@ -255,7 +255,7 @@ int lw_spectrum(const void* record, int32_t precision, int64_t n_pix, const lw_g
 
 /* Adjoint of lw_deposit_time_domain followed by lw_spectrum (reverse-mode
  * gradient of a loss L(S)).  Given g = dL/dS [n_pix][n_bins/2+1] (float64,
- * device) and X_save written by lw_spectrum with LW_FP64, adds to
+ * device) and X_save written by lw_spectrum with the same precision, adds to
  *   dL_dr, dL_dbeta, dL_dbeta_dot   float64 [n_e][n_s+1][3] (device, caller-zeroed)
  * the gradient of L with respect to every sample's position, velocity and
  * acceleration.  The record gradient is
@@ -267,7 +267,11 @@ int lw_spectrum(const void* record, int32_t precision, int64_t n_pix, const lw_g
  * with respect to beta and beta_dot.  L is piecewise smooth in the samples
  * (grid points entering or leaving an interval change its slope but not its
  * value); the result is the derivative on the current piece.
- *   precision    LW_FP64 (the FP64 section must exist)
+ *   precision    LW_FP64, or one of the LW_MIXED* modes (X_save then float2): the
+ *                advanced times and bin coordinates in FP64, fields, weights and the
+ *                chain rule in FP32 with the record gradient scaled by a power of two
+ *                (FP32 range: fields up to ~1e30 /s, 1 - n.beta above ~1e-5); the
+ *                FP64 section must exist in both cases
  *   field_flags  LW_FIELD_ACCEL
  *   q            particle charge [C] (as passed to lw_spectrum)
  *   ws           device scratch (NULL = size query): dL/drec, twiddles and,

@@ -29,17 +29,28 @@ Q_E = 1.602176634e-19
 M_E = 9.1093837015e-31
 
 
+def _sections(precision):
+    """Trajectory sections a forward in `precision` and its adjoint read (the adjoint
+    always reads the FP64 samples)."""
+    if precision == lw.LW_FP64:
+        return lw.LW_SECTION_FP64
+    return lw.LW_SECTION_FP64 | lw.LW_SECTION_MIXED
+
+
 class LWSpectrum(torch.autograd.Function):
-    """S[m][l] (FP64) of trajectories (t, r, beta, beta_dot) for a detector and grid."""
+    """S[m][l] of trajectories (t, r, beta, beta_dot) for a detector and grid: FP64 with
+    `precision` LW_FP64 (the default), FP32 with a mixed mode (mixed deposit and spectrum,
+    mixed-precision adjoint)."""
 
     @staticmethod
-    def forward(ctx, t, r, beta, beta_dot, det: "lw.Detector", grid: "lw.Grid", q: float = Q_E):
+    def forward(ctx, t, r, beta, beta_dot, det: "lw.Detector", grid: "lw.Grid", q: float = Q_E,
+                precision: int = lw.LW_FP64):
         traj = lw.lw_trajectories_upload(t.detach(), r.detach(), beta.detach(),
-                                         beta_dot.detach(), sections=lw.LW_SECTION_FP64,
+                                         beta_dot.detach(), sections=_sections(precision),
                                          device=det.n_hat.device)
-        rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
-        S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, q=q, want_X=True)
-        ctx.traj, ctx.det, ctx.grid, ctx.q = traj, det, grid, q
+        rec = lw.lw_deposit_time_domain(traj, det, grid, precision)
+        S, X = lw.lw_spectrum(rec, precision, det.n_pix, grid, q=q, want_X=True)
+        ctx.traj, ctx.det, ctx.grid, ctx.q, ctx.precision = traj, det, grid, q, precision
         ctx.save_for_backward(X)
         return S
 
@@ -47,20 +58,22 @@ class LWSpectrum(torch.autograd.Function):
     def backward(ctx, gS):
         (X,) = ctx.saved_tensors
         g_r, g_b, g_a = lw.lw_spectrum_grad(ctx.traj, ctx.det, ctx.grid, X, gS.contiguous(),
-                                            q=ctx.q)
-        return None, g_r, g_b, g_a, None, None, None
+                                            q=ctx.q, precision=ctx.precision)
+        return None, g_r, g_b, g_a, None, None, None, None
 
 
 class PushSpectrum(torch.autograd.Function):
-    """S[m][l] (FP64) of electrons pushed by the library's Boris kernel (lw_boris_push) from
+    """S[m][l] of electrons pushed by the library's Boris kernel (lw_boris_push) from
     (r0, u0) through the Gaussian laser (lam, a0, w0, fwhm), as a function of u0 [n_e, 3] and
-    the 0-d tensors a0 and w0.  Backward: lw_spectrum_grad (deposit and FFT transposed) then
+    the 0-d tensors a0 and w0; FP64 with `precision` LW_FP64, FP32 with a mixed mode.
+    Backward: lw_spectrum_grad (deposit and FFT transposed, in the forward's precision) then
     lw_boris_push_grad (the push differentiated in forward mode along u0, a0 and w0) -- every
     step in the library's kernels."""
 
     @staticmethod
     def forward(ctx, u0, a0, w0, r0, lam: float, fwhm: float, t_start: float, t_end: float,
-                n_steps: int, det: "lw.Detector", grid: "lw.Grid", q: float = Q_E):
+                n_steps: int, det: "lw.Detector", grid: "lw.Grid", q: float = Q_E,
+                precision: int = lw.LW_FP64):
         dev = u0.device
         n_e = u0.shape[0]
         dt = (t_end - t_start) / n_steps
@@ -71,10 +84,10 @@ class PushSpectrum(torch.autograd.Function):
         r0 = r0.detach().to(torch.float64).contiguous()
         u0d = u0.detach().to(torch.float64).contiguous()
         lw.lw_boris_push(r0.clone(), u0d.clone(), t_start, dt, n_steps, laser, t, R, B, A)
-        traj = lw.lw_trajectories_upload(t, R, B, A, sections=lw.LW_SECTION_FP64, device=dev)
-        rec = lw.lw_deposit_time_domain(traj, det, grid, lw.LW_FP64)
-        S, X = lw.lw_spectrum(rec, lw.LW_FP64, det.n_pix, grid, q=q, want_X=True)
-        ctx.traj, ctx.det, ctx.grid, ctx.q = traj, det, grid, q
+        traj = lw.lw_trajectories_upload(t, R, B, A, sections=_sections(precision), device=dev)
+        rec = lw.lw_deposit_time_domain(traj, det, grid, precision)
+        S, X = lw.lw_spectrum(rec, precision, det.n_pix, grid, q=q, want_X=True)
+        ctx.traj, ctx.det, ctx.grid, ctx.q, ctx.precision = traj, det, grid, q, precision
         ctx.push = (t_start, dt, n_steps, laser)
         ctx.save_for_backward(X, r0, u0d)
         return S
@@ -83,10 +96,11 @@ class PushSpectrum(torch.autograd.Function):
     def backward(ctx, gS):
         X, r0, u0 = ctx.saved_tensors
         g_r, g_b, g_a = lw.lw_spectrum_grad(ctx.traj, ctx.det, ctx.grid, X, gS.contiguous(),
-                                            q=ctx.q)
+                                            q=ctx.q, precision=ctx.precision)
         t_start, dt, n_steps, laser = ctx.push
         du0, dlaser = lw.lw_boris_push_grad(r0, u0, t_start, dt, n_steps, laser, g_r, g_b, g_a)
-        return (du0, dlaser[0], dlaser[1], None, None, None, None, None, None, None, None, None)
+        return (du0, dlaser[0], dlaser[1], None, None, None, None, None, None, None, None, None,
+                None)
 
 
 def band_mask(grid: "lw.Grid", omega_center: float, rel_half_width: float = 0.05):

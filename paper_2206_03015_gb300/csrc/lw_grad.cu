@@ -1,4 +1,4 @@
-// Adjoint of lw_deposit_time_domain followed by lw_spectrum (FP64).
+// Adjoint of lw_deposit_time_domain followed by lw_spectrum (FP64, and mixed precision below).
 //
 // Given g = dL/dS and the saved X' = sqrt(K) dt_u X, the record gradient is
 //   dL/drec_c[j] = 2 sqrt(K) dt_u Re( sum_{l=0}^{N/2} g_l conj(X'_c(l)) e^{+2 pi i j l/N} ),
@@ -26,7 +26,8 @@ namespace {
 // ------------------------------------------------------------ adjoint FFT
 
 struct AdjLoader {
-    const double2* X;     // [n_pix][3][nl]
+    const double2* X;     // [n_pix][3][nl] (FP64 forward)
+    const float2* Xf;     // the same from a mixed-precision forward (X unused when set)
     const double* g;      // [n_pix][nl]
     int64_t rows;         // 3 * n_pix
     int64_t nl;
@@ -39,7 +40,14 @@ struct AdjLoader {
             return h;
         }
         const int64_t m = row / 3;
-        const double2 x = X[row * nl + l];
+        double2 x;
+        if (Xf) {
+            const float2 xf = Xf[row * nl + l];
+            x.x = xf.x;
+            x.y = xf.y;
+        } else {
+            x = X[row * nl + l];
+        }
         const double s = two_sigma * g[m * nl + l];
         h.x = s * x.x;
         h.y = -s * x.y;
@@ -147,6 +155,8 @@ struct AdjArgs {
     double t_min, dt_u, inv_dtu;
     int64_t n_bins;
     const double* dLdrec;   // [n_pix][3][n_bins]
+    const float* dLdrec_f;  // mixed: dLdrec * 2^-e in FP32 (|values| < 2)
+    const double* rscale;   // mixed: 2^e (device scalar)
     double* g_r;
     double* g_beta;
     double* g_bdot;
@@ -323,6 +333,231 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_kernel(AdjArgs p) {
     }
 }
 
+// ------------------------------------------------------------ mixed-precision adjoint
+//
+// The same transpose with the advanced times and bin coordinates in FP64 (as every mixed
+// deposit) and everything else in FP32: the fields in the stable form
+// D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp, the weights from bin coordinates
+// relative to the step's first grid point, the sums over grid points and the per-sample
+// chain rule.  The record gradient enters scaled by a power of two 2^-e (|values| < 2,
+// e from its largest magnitude), so that its products with fields of up to ~1e30 /s stay
+// in FP32 range; the warp sums are unscaled in FP64 before the FP64 atomics.
+
+// largest |dL/drec| as ordered bits (non-negative doubles compare as integers)
+__global__ void adj_absmax_kernel(const double* __restrict__ R, int64_t n,
+                                  unsigned long long* __restrict__ mx) {
+    unsigned long long v = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(R[i]));
+        v = b > v ? b : v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
+}
+
+// 2^e >= the largest |dL/drec| / 2 (1 when it is zero or not finite)
+__device__ __forceinline__ int adj_exponent(unsigned long long mx) {
+    const int e = (int)(mx >> 52) - 1023;
+    return (mx == 0 || e > 1000 || e < -1000) ? 0 : e;
+}
+
+__global__ void adj_to_f32_kernel(const double* __restrict__ R, int64_t n,
+                                  const unsigned long long* __restrict__ mx,
+                                  float* __restrict__ Rf, double* __restrict__ rscale) {
+    const int e = adj_exponent(*mx);
+    const double down = ldexp(1.0, -e);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Rf[i] = (float)(R[i] * down);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rscale = ldexp(1.0, e);
+}
+
+struct NF {   // a pixel direction in FP32 with 1 - n_z kept exactly
+    float x, y, z, omz;
+};
+
+// acceleration field (n - beta) (n . bdot) - D bdot) / D^3 in FP32; zero when |beta| >= 1
+// (b.w == 0) or D <= 0
+__device__ __forceinline__ void field_acc_f32(const NF& n, float4 b, float4 a, float F[3]) {
+    const float D = fmaf(-n.y, b.y, fmaf(-n.x, b.x, fmaf(n.z, b.z, n.omz)));
+    const float mx = n.x - b.x, my = n.y - b.y, mz = b.z - n.omz;
+    const float nbd = fmaf(n.z, a.z, fmaf(n.y, a.y, n.x * a.x));
+    const float iD = __fdividef(1.0f, D);
+    const float iD3 = (b.w != 0.0f && D > 0.0f) ? iD * iD * iD : 0.0f;
+    F[0] = fmaf(mx, nbd, -D * a.x) * iD3;
+    F[1] = fmaf(my, nbd, -D * a.y) * iD3;
+    F[2] = fmaf(mz, nbd, -D * a.z) * iD3;
+}
+
+// (dL/dF, dL/du_a) of one sample -> (dL/du_a n, dL/dbeta, dL/dbdot) in FP32, on the scale
+// of the record gradient; dL/dr = -(dL/du_a) n / (c0 dt_u) is completed by the caller
+__device__ __forceinline__ void sample_chain_f32(const NF& n, float4 b, float4 a,
+                                                 const float G[3], float gu, float o[9]) {
+    o[0] = gu * n.x;
+    o[1] = gu * n.y;
+    o[2] = gu * n.z;
+    const float D = fmaf(-n.y, b.y, fmaf(-n.x, b.x, fmaf(n.z, b.z, n.omz)));
+    if (b.w == 0.0f || !(D > 0.0f)) {
+        for (int c = 3; c < 9; ++c) o[c] = 0.0f;
+        return;
+    }
+    const float iD = __fdividef(1.0f, D), iD3 = iD * iD * iD;
+    const float mx = n.x - b.x, my = n.y - b.y, mz = b.z - n.omz;
+    const float nbd = fmaf(n.z, a.z, fmaf(n.y, a.y, n.x * a.x));
+    const float bG = fmaf(a.z, G[2], fmaf(a.y, G[1], a.x * G[0]));
+    const float mG = fmaf(mz, G[2], fmaf(my, G[1], mx * G[0]));
+    const float Fx = fmaf(mx, nbd, -D * a.x) * iD3, Fy = fmaf(my, nbd, -D * a.y) * iD3,
+                Fz = fmaf(mz, nbd, -D * a.z) * iD3;
+    const float FG3 = 3.0f * fmaf(Fz, G[2], fmaf(Fy, G[1], Fx * G[0])) * iD;
+    o[3] = fmaf(fmaf(-nbd, G[0], n.x * bG), iD3, n.x * FG3);
+    o[4] = fmaf(fmaf(-nbd, G[1], n.y * bG), iD3, n.y * FG3);
+    o[5] = fmaf(fmaf(-nbd, G[2], n.z * bG), iD3, n.z * FG3);
+    o[6] = fmaf(n.x, mG, -D * G[0]) * iD3;
+    o[7] = fmaf(n.y, mG, -D * G[1]) * iD3;
+    o[8] = fmaf(n.z, mG, -D * G[2]) * iD3;
+}
+
+__device__ __forceinline__ void flush_sample_f32(const AdjArgs& p, bool act, const NF& n,
+                                                 int64_t k, int64_t i, float4 b, float4 a,
+                                                 const float G[3], float gu, bool nonzero,
+                                                 double r_scale, double u_scale) {
+    if (!__any_sync(0xffffffffu, nonzero)) return;
+    float o[9];
+    if (nonzero && act) {
+        sample_chain_f32(n, b, a, G, gu, o);
+    } else {
+        for (int c = 0; c < 9; ++c) o[c] = 0.0f;
+    }
+    for (int c = 0; c < 9; ++c)
+        for (int s = 16; s > 0; s >>= 1) o[c] += __shfl_xor_sync(0xffffffffu, o[c], s);
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t sidx = 3 * (k * p.ns1 + i);
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(p.g_r + sidx + c, (double)o[c] * u_scale);
+            atomicAdd(p.g_beta + sidx + c, (double)o[3 + c] * r_scale);
+            atomicAdd(p.g_bdot + sidx + c, (double)o[6 + c] * r_scale);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs p) {
+    __shared__ double s_t[kAdjTile];
+    __shared__ double s_r[kAdjTile * 3];
+    __shared__ float4 s_b[kAdjTile];   // (beta_x, beta_y, 1 - beta_z, |beta| < 1)
+    __shared__ float4 s_a[kAdjTile];   // (beta_dot, 0)
+    const int64_t m = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    const bool active = m < p.n_pix;
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    if (active) {
+        nx = p.n_hat[3 * m];
+        ny = p.n_hat[3 * m + 1];
+        nz = p.n_hat[3 * m + 2];
+    }
+    NF nf;
+    nf.x = (float)nx;
+    nf.y = (float)ny;
+    nf.z = (float)nz;
+    nf.omz = (float)(1.0 - nz);
+    const double r_scale = *p.rscale;
+    // dL/dr = -(dL/du_a) n / (c0 dt_u), on the record gradient's scale
+    const double u_scale = -r_scale * p.inv_dtu * kInvC0;
+    const float* R = p.dLdrec_f + (active ? m * 3 * p.n_bins : 0);
+    const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
+    const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
+    for (int64_t k = k0; k < k1; ++k) {
+        const double* tk = p.t + (p.t_per_e ? k * p.ns1 : 0);
+        const double* rk = p.r + 3 * k * p.ns1;
+        const double* bk = p.beta + 3 * k * p.ns1;
+        const double* ak = p.bdot + 3 * k * p.ns1;
+        double ub = 0.0;
+        float Fb[3] = {0.0f, 0.0f, 0.0f};
+        int64_t fb_step = -1;
+        float Gc[3] = {0.0f, 0.0f, 0.0f}, guc = 0.0f;   // carry: sample i-1 so far
+        bool nzc = false;
+        float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), pa = pb;   // sample i-1
+        for (int64_t i0 = 0; i0 < p.ns1; i0 += kAdjTile) {
+            const int n = (int)min((int64_t)kAdjTile, p.ns1 - i0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += kAdjThreads) {
+                s_t[q] = tk[i0 + q];
+                s_r[3 * q] = rk[3 * (i0 + q)];
+                s_r[3 * q + 1] = rk[3 * (i0 + q) + 1];
+                s_r[3 * q + 2] = rk[3 * (i0 + q) + 2];
+                const double* bq = bk + 3 * (i0 + q);
+                const double* aq = ak + 3 * (i0 + q);
+                const double bb = __dadd_rn(__dadd_rn(__dmul_rn(bq[0], bq[0]),
+                                                      __dmul_rn(bq[1], bq[1])),
+                                            __dmul_rn(bq[2], bq[2]));
+                s_b[q] = make_float4((float)bq[0], (float)bq[1], (float)(1.0 - bq[2]),
+                                     bb < 1.0 ? 1.0f : 0.0f);
+                s_a[q] = make_float4((float)aq[0], (float)aq[1], (float)aq[2], 0.0f);
+            }
+            __syncthreads();
+            for (int q = 0; q < n; ++q) {
+                const int64_t i = i0 + q;
+                const float4 cb = s_b[q], ca = s_a[q];
+                const double ta = advanced_time_fp64(nx, ny, nz, s_r[3 * q], s_r[3 * q + 1],
+                                                     s_r[3 * q + 2], s_t[q]);
+                const double ua = __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
+                float Gn[3] = {0.0f, 0.0f, 0.0f}, gun = 0.0f;   // contributions to sample i
+                bool nzn = false;
+                if (i > 0 && active && fabs(ua) < 4.0e18 && fabs(ub) < 4.0e18) {
+                    const double J0 = floor(ub);
+                    int64_t ja = (int64_t)J0 + 1, jz = (int64_t)floor(ua);
+                    if (ja < 0) ja = 0;
+                    if (jz > p.n_bins - 1) jz = p.n_bins - 1;
+                    if (ja <= jz) {
+                        if (fb_step != i - 1) field_acc_f32(nf, pb, pa, Fb);
+                        float Fa[3];
+                        field_acc_f32(nf, cb, ca, Fa);
+                        // bin coordinates relative to floor(u_b): exact in FP64, small in FP32
+                        const float xb = (float)(ub - J0), xa = (float)(ua - J0);
+                        const float iden = __fdividef(1.0f, xa - xb);
+                        const float d0 = Fa[0] - Fb[0], d1 = Fa[1] - Fb[1], d2 = Fa[2] - Fb[2];
+                        const int64_t jJ = (int64_t)J0;
+                        for (int64_t j = ja; j <= jz; ++j) {
+                            const float tj = (float)(j - jJ);
+                            const float wa = (xa - tj) * iden, wb = (tj - xb) * iden;
+                            const float R0 = R[j], R1 = R[p.n_bins + j], R2 = R[2 * p.n_bins + j];
+                            Gc[0] = fmaf(R0, wa, Gc[0]);
+                            Gc[1] = fmaf(R1, wa, Gc[1]);
+                            Gc[2] = fmaf(R2, wa, Gc[2]);
+                            Gn[0] = fmaf(R0, wb, Gn[0]);
+                            Gn[1] = fmaf(R1, wb, Gn[1]);
+                            Gn[2] = fmaf(R2, wb, Gn[2]);
+                            const float dw = fmaf(R2, d2, fmaf(R1, d1, R0 * d0)) * iden;
+                            gun = fmaf(-dw, wb, gun);
+                            guc = fmaf(-dw, wa, guc);
+                        }
+                        nzc = true;
+                        nzn = true;
+                        Fb[0] = Fa[0];
+                        Fb[1] = Fa[1];
+                        Fb[2] = Fa[2];
+                        fb_step = i;
+                    }
+                }
+                if (i > 0)
+                    flush_sample_f32(p, active, nf, k, i - 1, pb, pa, Gc, guc, nzc, r_scale,
+                                     u_scale);
+                Gc[0] = Gn[0];
+                Gc[1] = Gn[1];
+                Gc[2] = Gn[2];
+                guc = gun;
+                nzc = nzn;
+                ub = ua;
+                pb = cb;
+                pa = ca;
+            }
+        }
+        flush_sample_f32(p, active, nf, k, p.ns1 - 1, pb, pa, Gc, guc, nzc, r_scale, u_scale);
+    }
+}
+
 int pick_chunk(int64_t n_e, int64_t tiles) {
     const int64_t target = (int64_t)kSms * 16;
     int64_t chunk = (n_e * tiles + target - 1) / target;
@@ -341,7 +576,9 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
                                 const double* dL_dS, double q, double* dL_dr, double* dL_dbeta,
                                 double* dL_dbeta_dot, void* ws, size_t* ws_bytes, void* stream) {
     if (!traj || !det || !grid || !ws_bytes || !det->n_hat || det->n_pix < 1) return LW_EINVAL;
-    if (precision != LW_FP64) return LW_EUNSUPPORTED;
+    const bool mixed = precision == LW_MIXED || precision == LW_MIXED_KAHAN ||
+                       precision == LW_MIXED_F32 || precision == LW_MIXED_F32X4;
+    if (precision != LW_FP64 && !mixed) return LW_EUNSUPPORTED;
     if (field_flags != LW_FIELD_ACCEL) return LW_EUNSUPPORTED;
     if (!(traj->sections & LW_SECTION_FP64)) return LW_EINVAL;
     const int64_t N = grid->n_bins;
@@ -355,7 +592,9 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
     const size_t rec_bytes = align256(sizeof(double) * (size_t)(rows * N));
     const size_t tw_bytes = align256(sizeof(double2) * (size_t)N);
     const size_t y_bytes = direct ? 0 : align256(sizeof(double2) * (size_t)(pairs * N));
-    const size_t need = rec_bytes + tw_bytes + y_bytes;
+    // mixed: the scaled FP32 record gradient, its largest magnitude and the scale
+    const size_t f_bytes = mixed ? align256(sizeof(float) * (size_t)(rows * N)) + 256 : 0;
+    const size_t need = rec_bytes + tw_bytes + y_bytes + f_bytes;
     if (!ws) {
         *ws_bytes = need;
         return LW_OK;
@@ -372,7 +611,8 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
     double2* Y = reinterpret_cast<double2*>(base + rec_bytes + tw_bytes);
     const double K = q * q / (16.0 * kPi * kPi * kPi * kEps0 * kC0);
     AdjLoader ld;
-    ld.X = static_cast<const double2*>(X_save);
+    ld.X = mixed ? nullptr : static_cast<const double2*>(X_save);
+    ld.Xf = mixed ? static_cast<const float2*>(X_save) : nullptr;
     ld.g = dL_dS;
     ld.rows = rows;
     ld.nl = N / 2 + 1;
@@ -431,6 +671,23 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
     const int64_t tiles = (det->n_pix + kAdjThreads - 1) / kAdjThreads;
     a.e_chunk = pick_chunk(traj->n_e, tiles);
     dim3 g((unsigned)tiles, (unsigned)((traj->n_e + a.e_chunk - 1) / a.e_chunk));
-    adj_deposit_kernel<<<g, kAdjThreads, 0, st>>>(a);
+    if (!mixed) {
+        adj_deposit_kernel<<<g, kAdjThreads, 0, st>>>(a);
+        return launch_status();
+    }
+    char* fbase = base + rec_bytes + tw_bytes + y_bytes;
+    float* Rf = reinterpret_cast<float*>(fbase);
+    unsigned long long* mx =
+        reinterpret_cast<unsigned long long*>(fbase + align256(sizeof(float) * (size_t)(rows * N)));
+    double* rscale = reinterpret_cast<double*>(mx + 1);
+    if (cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st) != cudaSuccess) return LW_ECUDA;
+    const int64_t n_rec = rows * N;
+    const int rg = (int)std::min<int64_t>((n_rec + 255) / 256, (int64_t)kSms * 8);
+    adj_absmax_kernel<<<rg, 256, 0, st>>>(dLdrec, n_rec, mx);
+    adj_to_f32_kernel<<<rg, 256, 0, st>>>(dLdrec, n_rec, mx, Rf, rscale);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    a.dLdrec_f = Rf;
+    a.rscale = rscale;
+    adj_deposit_mixed_kernel<<<g, kAdjThreads, 0, st>>>(a);
     return launch_status();
 }

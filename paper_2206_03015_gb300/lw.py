@@ -373,29 +373,33 @@ def lw_spectrum(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E, 
 
 
 def lw_spectrum_grad(traj: Trajectories, det: Detector, grid: Grid, X_save, dL_dS,
-                     q: float = Q_E, out=None, field_flags: int = LW_FIELD_ACCEL):
-    """Adjoint of deposit + spectrum (FP64).  X_save: complex128 [n_pix][3][n_bins/2+1]
-    from lw_spectrum(..., want_X=True); dL_dS: float64 [n_pix][n_bins/2+1].
-    Returns (dL/dr, dL/dbeta, dL/dbeta_dot), each float64 [n_e][n_s+1][3]
-    (added to ``out`` when given)."""
+                     q: float = Q_E, out=None, field_flags: int = LW_FIELD_ACCEL,
+                     precision: int | None = None):
+    """Adjoint of deposit + spectrum.  X_save: [n_pix][3][n_bins/2+1] from
+    lw_spectrum(..., want_X=True), complex128 for LW_FP64 or complex64 for a mixed mode;
+    precision defaults to LW_FP64 or LW_MIXED after X_save's type.  dL_dS: float64
+    [n_pix][n_bins/2+1].  Returns (dL/dr, dL/dbeta, dL/dbeta_dot), each float64
+    [n_e][n_s+1][3] (added to ``out`` when given)."""
     lib = load()
     dev = det.n_hat.device
     shape = (traj.n_e, traj.n_s + 1, 3)
     if out is None:
         out = tuple(torch.zeros(shape, dtype=torch.float64, device=dev) for _ in range(3))
     X = torch.view_as_real(X_save.contiguous()) if X_save.is_complex() else X_save.contiguous()
-    assert X.dtype == torch.float64
+    if precision is None:
+        precision = LW_FP64 if X.dtype == torch.float64 else LW_MIXED
+    assert X.dtype == (torch.float64 if precision == LW_FP64 else torch.float32)
     g = dL_dS.to(torch.float64).contiguous()
     d = det.c()
     gr = grid.c()
     nbytes = ctypes.c_size_t(0)
     _check("lw_spectrum_grad", lib.lw_spectrum_grad(ctypes.byref(traj.view), ctypes.byref(d),
-                                                    ctypes.byref(gr), LW_FP64, field_flags, None,
+                                                    ctypes.byref(gr), precision, field_flags, None,
                                                     None, q, None, None, None, None,
                                                     ctypes.byref(nbytes), None))
     ws = _aligned_bytes(nbytes.value, dev)
     _check("lw_spectrum_grad", lib.lw_spectrum_grad(ctypes.byref(traj.view), ctypes.byref(d),
-                                                    ctypes.byref(gr), LW_FP64, field_flags,
+                                                    ctypes.byref(gr), precision, field_flags,
                                                     _ptr(X), _ptr(g), q, _ptr(out[0]),
                                                     _ptr(out[1]), _ptr(out[2]), _ptr(ws),
                                                     ctypes.byref(nbytes), _stream()))

@@ -105,6 +105,37 @@ def test_spectrum_grad_matches_oracle_gradient(t_per_electron):
                                                                np.abs(o).max())
 
 
+@pytest.mark.parametrize("precision", [lw.LW_MIXED_F32X4, lw.LW_MIXED])
+@pytest.mark.parametrize("t_per_electron", [False, True])
+def test_mixed_spectrum_grad_matches_oracle_gradient(t_per_electron, precision):
+    """The mixed-precision adjoint (FP64 advanced times and bins, FP32 fields, weights and
+    chain rule, X' from the mixed forward) against the oracle's chain-rule gradient:
+    element-wise within 1e-4 of the largest element, 2e-5 relative L2 per array."""
+    tr = simple.random_smooth(4, 90, 2e-18, 41, gamma=6.0, amp=0.4,
+                              t_per_electron=t_per_electron)
+    n_hat = _dirs(7, 5, 0.25)
+    lo, hi = oracle.grid_bounds(tr.t, tr.r, n_hat)
+    grid = lw.Grid(lo - 2.5 * (hi - lo) / 500, (hi - lo) / 500, 512)
+    rng = np.random.Generator(np.random.PCG64(17))
+    w = rng.uniform(0.2, 2.0, size=(7, 257))
+    ref = oracle.tdm_grad(tr.t, tr.r, tr.beta, tr.beta_dot, n_hat, grid.t_min, grid.dt_u,
+                          grid.n_bins, w)
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
+                                     sections=lw.LW_SECTION_FP64 | lw.LW_SECTION_MIXED, block=32)
+    det = lw.Detector(n_hat)
+    rec = lw.lw_deposit_time_domain(traj, det, grid, precision)
+    S, X = lw.lw_spectrum(rec, precision, det.n_pix, grid, want_X=True)
+    assert X.dtype == torch.complex64
+    got = lw.lw_spectrum_grad(traj, det, grid, X, torch.from_numpy(w).cuda(), precision=precision)
+    torch.cuda.synchronize()
+    for name, g, o in zip(("r", "beta", "beta_dot"), got, ref):
+        g = g.cpu().numpy()
+        assert np.all(np.isfinite(g)), name
+        assert np.abs(g - o).max() <= 1e-4 * np.abs(o).max(), (name, np.abs(g - o).max(),
+                                                               np.abs(o).max())
+        assert np.linalg.norm(g - o) <= 2e-5 * np.linalg.norm(o), name
+
+
 def _c4_small():
     laser = GaussianLaser(lam=1e-6, a0=1.0, w0=20e-6, fwhm=10e-15)
     n_e, gamma = 6, 60.0
@@ -193,3 +224,36 @@ def test_band_energy_gradient_wrt_initial_conditions_and_laser():
     for name, gs, fd in checks:
         for g in gs:   # torch-autograd pusher, then the library's forward-mode kernel
             assert abs(g - fd) <= TOL * abs(fd), (name, g, fd)
+
+
+def test_mixed_push_spectrum_gradient_matches_fp64():
+    """Config 4's chain in mixed precision (mixed deposit and spectrum, mixed adjoint) against
+    the FP64 chain on the small config-4 case: the loss within 1e-5, the gradients with
+    respect to u0 (relative L2), a0 and w0 within 1e-4 (the FP64 chain is checked against
+    finite differences of the oracle above)."""
+    laser, r0, u0, t0, t1, n_s, gamma = _c4_small()
+    n_hat = _dirs(9, 11, 0.1 / gamma)
+    tr0 = boris_trajectories(r0, u0, laser, t0, t1, n_s)
+    lo, hi = oracle.grid_bounds(tr0.t, tr0.r, n_hat)
+    dt_u = (hi - lo) / 2048
+    grid = lw.Grid(lo - 0.5 * dt_u, dt_u, 8192)
+    mask = band_mask(grid, doppler_fundamental(gamma, laser.lam, laser.a0), 0.05)
+    det = lw.Detector(n_hat)
+    dev = torch.device("cuda")
+    out = {}
+    for prec in (lw.LW_FP64, lw.LW_MIXED_F32X4):
+        u = torch.tensor(u0, device=dev, requires_grad=True)
+        a0 = torch.tensor(laser.a0, dtype=torch.float64, device=dev, requires_grad=True)
+        w0 = torch.tensor(laser.w0, dtype=torch.float64, device=dev, requires_grad=True)
+        S = PushSpectrum.apply(u, a0, w0, torch.tensor(r0, device=dev), laser.lam, laser.fwhm,
+                               t0, t1, n_s, det, grid, 1.602176634e-19, prec)
+        L = band_energy(S.to(torch.float64), grid, mask)
+        L.backward()
+        torch.cuda.synchronize()
+        out[prec] = (float(L), u.grad.clone(), float(a0.grad), float(w0.grad))
+    L64, gu64, ga64, gw64 = out[lw.LW_FP64]
+    L32, gu32, ga32, gw32 = out[lw.LW_MIXED_F32X4]
+    assert abs(L32 / L64 - 1.0) < 1e-5
+    assert float(torch.linalg.norm(gu32 - gu64) / torch.linalg.norm(gu64)) < 1e-4
+    assert abs(ga32 - ga64) <= 1e-4 * abs(ga64)
+    assert abs(gw32 - gw64) <= 1e-4 * abs(gw64)
