@@ -267,11 +267,12 @@ int lw_spectrum(const void* record, int32_t precision, int64_t n_pix, const lw_g
  * with respect to beta and beta_dot.  L is piecewise smooth in the samples
  * (grid points entering or leaving an interval change its slope but not its
  * value); the result is the derivative on the current piece.
- *   precision    LW_FP64, or one of the LW_MIXED* modes (X_save then float2): the
- *                advanced times and bin coordinates in FP64, fields, weights and the
- *                chain rule in FP32 with the record gradient scaled by a power of two
- *                (FP32 range: fields up to ~1e30 /s, 1 - n.beta above ~1e-5); the
- *                FP64 section must exist in both cases
+ *   precision    LW_FP64, or one of the LW_MIXED* modes (X_save then float2): bin
+ *                coordinates in FP64 at every 64th sample and in FP32 relative to it
+ *                in between, fields, weights and the chain rule in FP32 with the
+ *                record gradient scaled by a power of two (FP32 range: fields up to
+ *                ~1e30 /s, 1 - n.beta above ~1e-5); the FP64 section must exist in
+ *                both cases
  *   field_flags  LW_FIELD_ACCEL
  *   q            particle charge [C] (as passed to lw_spectrum)
  *   ws           device scratch (NULL = size query): dL/drec, twiddles and,

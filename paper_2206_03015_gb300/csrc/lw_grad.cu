@@ -335,8 +335,11 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_kernel(AdjArgs p) {
 
 // ------------------------------------------------------------ mixed-precision adjoint
 //
-// The same transpose with the advanced times and bin coordinates in FP64 (as every mixed
-// deposit) and everything else in FP32: the fields in the stable form
+// The same transpose in mixed precision: the bin coordinate of each tile's first sample in
+// FP64 and, within the tile of 64 samples, each sample's as an integer plus an FP32
+// fraction advanced by the step's FP32 increment (from FP64-differenced samples), so the
+// weights are computed from numbers of the size of a step; everything else in FP32:
+// the fields in the stable form
 // D = (1 - n_z) + n_z (1 - beta_z) - n_perp . beta_perp, the weights from bin coordinates
 // relative to the step's first grid point, the sums over grid points and the per-sample
 // chain rule.  The record gradient enters scaled by a power of two 2^-e (|values| < 2,
@@ -444,11 +447,18 @@ __device__ __forceinline__ void flush_sample_f32(const AdjArgs& p, bool act, con
     }
 }
 
+// Half-width of the band around an integer inside which a sample's bin coordinate is
+// recomputed in FP64: far above the FP32 chain's rounding over a tile (64 steps of a few
+// ulps of the step's terms).
+constexpr float kAdjGuard = 1.0f / (1 << 12);
+
 __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs p) {
-    __shared__ double s_t[kAdjTile];
-    __shared__ double s_r[kAdjTile * 3];
+    // one tile of samples i0 .. i0 + kAdjTile - 1, staged once per CTA: each sample's step
+    // from the previous one (FP64 differences rounded to FP32) and its fields' inputs
+    __shared__ float4 s_d[kAdjTile];   // (tau_i - tau_i-1, r_i - r_i-1), tau = t - z/c0
     __shared__ float4 s_b[kAdjTile];   // (beta_x, beta_y, 1 - beta_z, |beta| < 1)
     __shared__ float4 s_a[kAdjTile];   // (beta_dot, 0)
+    __shared__ double s_anc[4];        // (t, r) of sample i0
     const int64_t m = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
     const bool active = m < p.n_pix;
     double nx = 0.0, ny = 0.0, nz = 1.0;
@@ -462,10 +472,28 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
     nf.y = (float)ny;
     nf.z = (float)nz;
     nf.omz = (float)(1.0 - nz);
+    // bin coordinate u = (t_a - t_min)/dt_u = (tau - t_min)/dt_u + w . r with the pixel's
+    // slope w = (-n_x, -n_y, 1 - n_z) / (c0 dt_u): in FP64 at each tile's first sample; from
+    // there on as J + f (integer, FP32 fraction) advanced by each step's FP32 increment
+    // s dtau + w . dr, so that the weights see small numbers
+    const double sw = kInvC0 * p.inv_dtu;
+    const double wx = -nx * sw, wy = -ny * sw, wz = (1.0 - nz) * sw;
+    const float s32 = (float)p.inv_dtu, wx32 = (float)wx, wy32 = (float)wy, wz32 = (float)wz;
     const double r_scale = *p.rscale;
     // dL/dr = -(dL/du_a) n / (c0 dt_u), on the record gradient's scale
     const double u_scale = -r_scale * p.inv_dtu * kInvC0;
     const float* R = p.dLdrec_f + (active ? m * 3 * p.n_bins : 0);
+    // the FP64 adjoint's bin coordinate of a sample, and its split into floor + fraction
+    auto u_fp64 = [&](double t, double x, double y, double z) {
+        return __dmul_rn(__dsub_rn(advanced_time_fp64(nx, ny, nz, x, y, z, t), p.t_min),
+                         p.inv_dtu);
+    };
+    auto exact_coord = [&](double u, int64_t& Jo, float& fo) {
+        u = fmin(fmax(u, -1.0e15), 1.0e15);
+        const double fl = floor(u);
+        Jo = (int64_t)fl;
+        fo = (float)(u - fl);
+    };
     const int64_t k0 = (int64_t)blockIdx.y * p.e_chunk;
     const int64_t k1 = min(k0 + p.e_chunk, p.n_e);
     for (int64_t k = k0; k < k1; ++k) {
@@ -473,22 +501,27 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
         const double* rk = p.r + 3 * k * p.ns1;
         const double* bk = p.beta + 3 * k * p.ns1;
         const double* ak = p.bdot + 3 * k * p.ns1;
-        double ub = 0.0;
         float Fb[3] = {0.0f, 0.0f, 0.0f};
         int64_t fb_step = -1;
         float Gc[3] = {0.0f, 0.0f, 0.0f}, guc = 0.0f;   // carry: sample i-1 so far
         bool nzc = false;
         float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), pa = pb;   // sample i-1
+        int64_t J = 0;   // sample i-1 at J + f
+        float f = 0.0f;
         for (int64_t i0 = 0; i0 < p.ns1; i0 += kAdjTile) {
             const int n = (int)min((int64_t)kAdjTile, p.ns1 - i0);
             __syncthreads();
             for (int q = threadIdx.x; q < n; q += kAdjThreads) {
-                s_t[q] = tk[i0 + q];
-                s_r[3 * q] = rk[3 * (i0 + q)];
-                s_r[3 * q + 1] = rk[3 * (i0 + q) + 1];
-                s_r[3 * q + 2] = rk[3 * (i0 + q) + 2];
-                const double* bq = bk + 3 * (i0 + q);
-                const double* aq = ak + 3 * (i0 + q);
+                const int64_t i = i0 + q;
+                const double* rq = rk + 3 * i;
+                const double* bq = bk + 3 * i;
+                const double* aq = ak + 3 * i;
+                if (i > 0) {
+                    const double tau = tk[i] - rq[2] * kInvC0;
+                    const double taup = tk[i - 1] - rq[-1] * kInvC0;
+                    s_d[q] = make_float4((float)(tau - taup), (float)(rq[0] - rq[-3]),
+                                         (float)(rq[1] - rq[-2]), (float)(rq[2] - rq[-1]));
+                }
                 const double bb = __dadd_rn(__dadd_rn(__dmul_rn(bq[0], bq[0]),
                                                       __dmul_rn(bq[1], bq[1])),
                                             __dmul_rn(bq[2], bq[2]));
@@ -496,32 +529,60 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
                                      bb < 1.0 ? 1.0f : 0.0f);
                 s_a[q] = make_float4((float)aq[0], (float)aq[1], (float)aq[2], 0.0f);
             }
+            if (threadIdx.x == 0) {
+                s_anc[0] = tk[i0];
+                s_anc[1] = rk[3 * i0];
+                s_anc[2] = rk[3 * i0 + 1];
+                s_anc[3] = rk[3 * i0 + 2];
+            }
             __syncthreads();
+            // sample i0 with the FP64 adjoint's expression: J0 + f0
+            int64_t J0;
+            float f0;
+            exact_coord(u_fp64(s_anc[0], s_anc[1], s_anc[2], s_anc[3]), J0, f0);
             for (int q = 0; q < n; ++q) {
                 const int64_t i = i0 + q;
                 const float4 cb = s_b[q], ca = s_a[q];
-                const double ta = advanced_time_fp64(nx, ny, nz, s_r[3 * q], s_r[3 * q + 1],
-                                                     s_r[3 * q + 2], s_t[q]);
-                const double ua = __dmul_rn(__dsub_rn(ta, p.t_min), p.inv_dtu);
+                // sample i at Ji + fi: the tile's first from the FP64 anchor, the others
+                // advanced from sample i-1 by the step's FP32 increment, and recomputed in
+                // FP64 when the fraction lies within kAdjGuard of an integer, so that the
+                // floors -- which grid points a step holds -- are those of the FP64 adjoint
+                int64_t Ji;
+                float fi;
+                if (q == 0) {
+                    Ji = J0;
+                    fi = f0;
+                } else {
+                    const float4 d = s_d[q];
+                    float u = f + fmaf(wz32, d.w, fmaf(wy32, d.z, fmaf(wx32, d.y, s32 * d.x)));
+                    u = fminf(fmaxf(u, -1.0e9f), 1.0e9f);
+                    const float fl = floorf(u);
+                    Ji = J + (int64_t)fl;
+                    fi = u - fl;
+                    if (fi < kAdjGuard || fi > 1.0f - kAdjGuard) {
+                        const double* rq = rk + 3 * i;
+                        exact_coord(u_fp64(tk[i], rq[0], rq[1], rq[2]), Ji, fi);
+                    }
+                }
+                // the step (i-1, i] relative to Jf = J_(i-1): ub = f_(i-1), ua = u_i - Jf
+                const int64_t Jf = J, dJ = Ji - J;
+                const float ub = f;
+                const float ua = (dJ > -(1 << 24) && dJ < (1 << 24)) ? (float)dJ + fi : 1.0e9f;
                 float Gn[3] = {0.0f, 0.0f, 0.0f}, gun = 0.0f;   // contributions to sample i
                 bool nzn = false;
-                if (i > 0 && active && fabs(ua) < 4.0e18 && fabs(ub) < 4.0e18) {
-                    const double J0 = floor(ub);
-                    int64_t ja = (int64_t)J0 + 1, jz = (int64_t)floor(ua);
+                if (i > 0 && active) {
+                    int64_t ja = J + 1, jz = Ji;
                     if (ja < 0) ja = 0;
                     if (jz > p.n_bins - 1) jz = p.n_bins - 1;
                     if (ja <= jz) {
                         if (fb_step != i - 1) field_acc_f32(nf, pb, pa, Fb);
                         float Fa[3];
                         field_acc_f32(nf, cb, ca, Fa);
-                        // bin coordinates relative to floor(u_b): exact in FP64, small in FP32
-                        const float xb = (float)(ub - J0), xa = (float)(ua - J0);
-                        const float iden = __fdividef(1.0f, xa - xb);
+                        const float iden = __fdividef(1.0f, ua - ub);
                         const float d0 = Fa[0] - Fb[0], d1 = Fa[1] - Fb[1], d2 = Fa[2] - Fb[2];
-                        const int64_t jJ = (int64_t)J0;
                         for (int64_t j = ja; j <= jz; ++j) {
-                            const float tj = (float)(j - jJ);
-                            const float wa = (xa - tj) * iden, wb = (tj - xb) * iden;
+                            const float tj = (float)(j - Jf);
+                            const float wa = (ua - tj) * iden, wb = (tj - ub) * iden;
                             const float R0 = R[j], R1 = R[p.n_bins + j], R2 = R[2 * p.n_bins + j];
                             Gc[0] = fmaf(R0, wa, Gc[0]);
                             Gc[1] = fmaf(R1, wa, Gc[1]);
@@ -549,7 +610,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
                 Gc[2] = Gn[2];
                 guc = gun;
                 nzc = nzn;
-                ub = ua;
+                J = Ji;
+                f = fi;
                 pb = cb;
                 pa = ca;
             }

@@ -251,48 +251,57 @@ __global__ void push_kernel(double* __restrict__ r, double* __restrict__ u, int6
 }
 
 // Gradient of a loss L(samples) with respect to each electron's initial momentum u0 and
-// the laser's a0 and w0, by forward-mode differentiation of the push: every electron is
-// pushed again carrying the derivatives of its state along u0_x, u0_y, u0_z, a0 and w0
-// (Dual<5>), and each sample's derivatives are contracted with dL/d(r, beta, beta_dot)
-// of that sample.  Per-electron a0 and w0 parts are added to dL_dlaser with FP64 atomics.
+// the laser's a0 and w0, by forward-mode differentiation of the push: one thread per
+// (electron, direction) pushes the electron again carrying the derivative of its state
+// along one of u0_x, u0_y, u0_z, a0 and w0 (Dual<1>) and contracts each sample's
+// derivative with dL/d(r, beta, beta_dot) of that sample.  Five threads per electron
+// rather than one thread with all five directions: the push is a sequential FP64 chain
+// per electron, and GB300's FP64 rate per SM sub-partition makes a single warp's
+// instructions slow, so the work is spread over five times as many warps.  Per-electron
+// a0 and w0 parts are added to dL_dlaser with FP64 atomics.
 constexpr int kTan = 5;
 __global__ void push_tangent_kernel(const double* __restrict__ r0, const double* __restrict__ u0,
-                                    int64_t n_e, double t0, double dt, int n_steps,
-                                    LaserT<Dual<kTan>> L, double qm,
+                                    int64_t n_e, double t0, double dt, int n_steps, Laser L0,
+                                    double e0_per_a0, double zr_per_w0, double qm,
                                     const double* __restrict__ g_r, const double* __restrict__ g_b,
                                     const double* __restrict__ g_a, double* __restrict__ dL_du0,
                                     double* __restrict__ dL_dlaser) {
-    using D = Dual<kTan>;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_e;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    using D = Dual<1>;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_e * kTan;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / kTan;
+        const int dir = (int)(t - k * kTan);   // 0..2: u0 components, 3: a0, 4: w0
+        LaserT<D> L;
+        L.omega = L0.omega;
+        L.k = L0.k;
+        L.sigma = L0.sigma;
+        L.E0 = D{L0.E0, {dir == 3 ? e0_per_a0 : 0.0}};
+        L.zR = D{L0.zR, {dir == 4 ? zr_per_w0 : 0.0}};
+        L.w0 = D{L0.w0, {dir == 4 ? 1.0 : 0.0}};
         D x[3], v[3];
         for (int c = 0; c < 3; ++c) {
-            x[c] = mk<kTan>(r0[3 * k + c]);
-            v[c] = mk<kTan>(u0[3 * k + c]);
-            v[c].d[c] = 1.0;   // directions 0..2: u0
+            x[c] = mk<1>(r0[3 * k + c]);
+            v[c] = mk<1>(u0[3 * k + c]);
+            v[c].d[0] = dir == c ? 1.0 : 0.0;
         }
-        double acc[kTan];
-#pragma unroll
-        for (int i = 0; i < kTan; ++i) acc[i] = 0.0;
+        double acc = 0.0;
         const int64_t base = k * (int64_t)(n_steps + 1);
-        auto contract = [&](int64_t o, double t) {
+        auto contract = [&](int64_t o, double tt) {
             D b[3], a[3];
-            sample(L, qm, x, v, t, b, a);
-            for (int c = 0; c < 3; ++c) {
-                const double gr = g_r[3 * o + c], gb = g_b[3 * o + c], ga = g_a[3 * o + c];
-#pragma unroll
-                for (int i = 0; i < kTan; ++i)
-                    acc[i] = fma(gr, x[c].d[i], fma(gb, b[c].d[i], fma(ga, a[c].d[i], acc[i])));
-            }
+            sample(L, qm, x, v, tt, b, a);
+            for (int c = 0; c < 3; ++c)
+                acc = fma(g_r[3 * o + c], x[c].d[0],
+                          fma(g_b[3 * o + c], b[c].d[0], fma(g_a[3 * o + c], a[c].d[0], acc)));
         };
         contract(base, t0);
         for (int s = 0; s < n_steps; ++s) {
             boris_step(L, qm, dt, t0 + dt * (double)s, x, v);
             contract(base + s + 1, t0 + dt * (double)(s + 1));
         }
-        for (int c = 0; c < 3; ++c) dL_du0[3 * k + c] += acc[c];
-        atomicAdd(dL_dlaser, acc[3]);
-        atomicAdd(dL_dlaser + 1, acc[4]);
+        if (dir < 3)
+            dL_du0[3 * k + dir] += acc;
+        else
+            atomicAdd(dL_dlaser + (dir - 3), acc);
     }
 }
 
@@ -326,7 +335,9 @@ extern "C" int lw_boris_push(double* r, double* u, int64_t n_e, double t0, doubl
     cudaStream_t st = as_stream(stream);
     times_kernel<<<(n_steps + 256) / 256, 256, 0, st>>>(t_out, t0, dt, step0, n_steps);
     if (launch_status() != LW_OK) return LW_ECUDA;
-    const int threads = 128;
+    // one warp per block: a push is a sequential FP64 chain per electron, so the few
+    // warps of a small bunch are spread over as many SMs as possible
+    const int threads = 32;
     const int blocks = (int)((n_e + threads - 1) / threads);
     push_kernel<<<blocks, threads, 0, st>>>(r, u, n_e, t0, dt, step0, n_steps, L, charge / mass, r_out,
                                             beta_out, bdot_out);
@@ -343,19 +354,21 @@ extern "C" int lw_boris_push_grad(const double* r0, const double* u0, int64_t n_
     if (n_e < 1 || n_steps < 1 || !(dt > 0.0) || !isfinite(t0) || !(mass > 0.0))
         return LW_EINVAL;
     if (!(laser->lam > 0.0) || !(laser->w0 > 0.0) || !(laser->fwhm > 0.0)) return LW_EINVAL;
-    LaserT<Dual<kTan>> L;
+    Laser L;
     L.omega = 2.0 * kPi * kC0 / laser->lam;
     L.k = L.omega * kInvC0;
     L.sigma = laser->fwhm / (2.0 * sqrt(log(2.0)));
     const double e0_per_a0 = kMe * kC0 * L.omega / kQe;
-    L.E0 = Dual<kTan>{laser->a0 * e0_per_a0, {0.0, 0.0, 0.0, e0_per_a0, 0.0}};   // direction 3: a0
-    L.zR = Dual<kTan>{kPi * laser->w0 * laser->w0 / laser->lam,
-                      {0.0, 0.0, 0.0, 0.0, 2.0 * kPi * laser->w0 / laser->lam}};  // direction 4: w0
-    L.w0 = Dual<kTan>{laser->w0, {0.0, 0.0, 0.0, 0.0, 1.0}};
-    const int threads = 64;
-    const int blocks = (int)((n_e + threads - 1) / threads);
+    L.E0 = laser->a0 * e0_per_a0;
+    L.zR = kPi * laser->w0 * laser->w0 / laser->lam;
+    L.w0 = laser->w0;
+    const double zr_per_w0 = 2.0 * kPi * laser->w0 / laser->lam;
+    // one warp per block: the warps spread over the SMs' sub-partitions
+    const int threads = 32;
+    const int64_t work = n_e * kTan;
+    const int blocks = (int)std::min<int64_t>((work + threads - 1) / threads, 1 << 20);
     push_tangent_kernel<<<blocks, threads, 0, as_stream(stream)>>>(
-        r0, u0, n_e, t0, dt, n_steps, L, charge / mass, dL_dr, dL_dbeta, dL_dbeta_dot, dL_du0,
-        dL_dlaser);
+        r0, u0, n_e, t0, dt, n_steps, L, e0_per_a0, zr_per_w0, charge / mass, dL_dr, dL_dbeta,
+        dL_dbeta_dot, dL_du0, dL_dlaser);
     return launch_status();
 }
