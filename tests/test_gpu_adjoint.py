@@ -1,5 +1,5 @@
-"""Adjoint (lw_spectrum_grad, FP64) against central finite differences of the
-CPU oracle and against the oracle's own gradient, and the end-to-end gradient
+"""Adjoint (lw_spectrum_grad, FP64 and mixed precision) against central finite differences
+of the CPU oracle and against the oracle's own gradient, and the end-to-end gradient
 of a band-integrated spectral yield with respect to initial momenta and the
 laser a0 / waist (differentiable
 Boris pusher + LWSpectrum) against finite differences of the oracle fed by
