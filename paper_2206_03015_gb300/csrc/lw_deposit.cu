@@ -582,6 +582,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
     const int64_t pix0 = tile * kSlots;
     unsigned act = 0;
     float wlo[PIX][3];   // slope lo parts of this thread's pixels (its anchors only)
+    float whi[PIX][3];   // and their hi parts (the copies in s_wh serve other lanes' jobs)
     __syncthreads();   // shared arrays may still be read by the previous unit
     if (threadIdx.x == 0) {
         for (int s = 0; s < kMixStages; ++s) mbar_init(&s_full[s], 1);
@@ -609,6 +610,9 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
         wlo[q][0] = wx.lo;
         wlo[q][1] = wy.lo;
         wlo[q][2] = wz.lo;
+        whi[q][0] = wx.hi;
+        whi[q][1] = wy.hi;
+        whi[q][2] = wz.hi;
     }
     __syncthreads();   // barriers initialised
     int bits = 0;
@@ -751,7 +755,8 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
                 for (int c = 0; c < 8; ++c) an0[c] = __shfl_sync(0xffffffffu, anc32[c], 0);
 #pragma unroll
                 for (int q = 0; q < PIX; ++q) {   // block 0's anchor is sample 0
-                    anchor_of(an0, s_wh[wslot + lane * PIX + q], q, Is[q], fs[q]);
+                    anchor_of(an0, make_float4(whi[q][0], whi[q][1], whi[q][2], 0.0f), q,
+                              Is[q], fs[q]);
                     const int fl = frac_floor(fs[q]);
                     const float fr = fs[q] - (float)fl;
                     jdone[q] = Is[q] + fl;
@@ -774,7 +779,7 @@ __device__ __forceinline__ int mixed_cta(const DepositArgs& p, int64_t tile, int
 #pragma unroll
             for (int q = 0; q < PIX; ++q) {
                 const int sl = wslot + lane * PIX + q;
-                const float4 wh = s_wh[sl];
+                const float4 wh = make_float4(whi[q][0], whi[q][1], whi[q][2], 0.0f);
                 int Ie = 0, jend;
                 float fe = 0.0f, xe;
                 if (end_anchor) {
