@@ -1017,7 +1017,9 @@ def main():
     ap.add_argument("--c5-nx", type=int, nargs=2, default=(16, 128))
     ap.add_argument("--c5-bins", type=int, nargs=2, default=(12, 17))
     ap.add_argument("--c5-record", default="f32", choices=["f32", "x4", "f64"])
-    ap.add_argument("--c5-budget-gb", type=float, default=200.0)
+    # resident data of a wave; building a variant also holds its FP64 trajectories and a
+    # tuning record, so the budget stays well below the device memory (150 of 277 GB)
+    ap.add_argument("--c5-budget-gb", type=float, default=150.0)
     ap.add_argument("--c5-tune-blocks", type=int, nargs="+", default=(256, 512))
     ap.add_argument("--c5-tune-chunks", type=int, nargs="+", default=(1, 4))
     args = ap.parse_args()
