@@ -367,23 +367,25 @@ def run_ours(args, rank, world, dist):
                                          "L2 reductions, FP32 FMA and shared loads measured "
                                          "in this run (paper_2206_03015_gb300/peaks)")
     result["clocks"] = clocks
-    # the other mixed record beside it (FP64 record when the FP32 one is timed)
-    if MIX != lw.LW_MIXED:
-        rec_64 = torch.empty(lw.record_shape(det, grid, lw.LW_MIXED)[0], dtype=torch.float64,
-                             device=dev)
-        S_64m = torch.empty_like(S_m)
+    # the other records beside it: FP64 (LW_MIXED) and compensated FP32 pairs
+    # (LW_MIXED_KAHAN), each the same step with that record
+    for prec2, key in ((lw.LW_MIXED, "mixed_fp64_record"), (lw.LW_MIXED_KAHAN, "mixed_kahan_record")):
+        if prec2 == MIX:
+            continue
+        shp2, dt2 = lw.record_shape(det, grid, prec2)
+        rec_2 = torch.empty(shp2, dtype=dt2, device=dev)
+        S_2 = torch.empty_like(S_m)
 
-        def step_mixed64(timed=False):
+        def step_mixed2(timed=False, prec2=prec2, rec_2=rec_2, S_2=S_2):
             traj = lw.lw_trajectories_upload(t_d, r_d, b_d, a_d, sections=lw.LW_SECTION_MIXED,
                                              block=args.block, device=dev, ws=ws_t)
-            lw.lw_deposit_time_domain(traj, det, grid, lw.LW_MIXED, record=rec_64,
-                                      status=status)
-            lw.lw_spectrum(rec_64, lw.LW_MIXED, det.n_pix, grid, ws=ws_s, out=S_64m)
+            lw.lw_deposit_time_domain(traj, det, grid, prec2, record=rec_2, status=status)
+            lw.lw_spectrum(rec_2, prec2, det.n_pix, grid, ws=ws_s, out=S_2)
 
-        ms_64m, _ = timed_loop(step_mixed64, args.steps, args.warmup)
-        result["mixed_fp64_record"] = {"ms_per_step": ms_64m / args.steps,
-                                       "value": n_job / (ms_64m / args.steps * 1e-3)}
-        del rec_64, S_64m
+        ms_2, _ = timed_loop(step_mixed2, args.steps, args.warmup)
+        result[key] = {"ms_per_step": ms_2 / args.steps,
+                       "value": n_job / (ms_2 / args.steps * 1e-3)}
+        del rec_2, S_2
     torch.cuda.synchronize()
     st_m = int(status.item())
 

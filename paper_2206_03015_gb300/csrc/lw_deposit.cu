@@ -1244,18 +1244,26 @@ __global__ void __launch_bounds__(kFp64Threads) deposit_fp64_jobs_kernel(Deposit
 
 template <int PIX, int ACC, int FL>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks) deposit_mixed_kernel(DepositArgs p) {
+    // the precision check launched after this grid (programmatic dependent launch) may
+    // start once every CTA of this grid has started: it fills the SMs of the last wave
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int bits = mixed_cta<PIX, ACC, FL, false>(p, blockIdx.x, blockIdx.y);
     block_status_or(p.status, bits);
 }
 
 // Precision check of a mixed deposit: the units of every `stride`-th electron chunk
-// (grid y = sampled chunks), evaluated without depositing.
+// (grid y = sampled chunks), evaluated without depositing.  Launched as a programmatic
+// dependent of the deposit, it runs beside the deposit's last CTAs and, before it ends,
+// waits for the deposit grid to complete (griddepcontrol.wait: its completion and memory
+// flush), so that work after it in the stream sees the finished record; without that
+// launch attribute the wait returns at once.
 template <int PIX, int FL>
 __global__ void __launch_bounds__(kMixThreads, kMixMinBlocks)
     deposit_check_kernel(DepositArgs p, int stride) {
     const int bits =
         mixed_cta<PIX, kAccF32X4, FL, true>(p, blockIdx.x, (int64_t)blockIdx.y * stride);
     block_status_or(p.status, bits & LW_ST_PRECISION);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Persistent form: CTAs pull (variant, pixel tile, electron chunk) units from a
@@ -1453,8 +1461,17 @@ extern "C" int lw_deposit_time_domain(const lw_traj* traj, const lw_detector* de
         if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return LW_ECUDA;
-        ck<<<dim3(g.x, (unsigned)((chunks + stride - 1) / stride)), kMixThreads, smem, st>>>(a,
-                                                                                          stride);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g.x, (unsigned)((chunks + stride - 1) / stride));
+        cfg.blockDim = dim3(kMixThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, ck, a, stride) != cudaSuccess) return LW_ECUDA;
     }
     return launch_status();
 }
