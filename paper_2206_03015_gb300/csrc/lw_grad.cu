@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
     // dL/dr = -(dL/du_a) n / (c0 dt_u), on the record gradient's scale
     const double u_scale = -r_scale * p.inv_dtu * kInvC0;
     const float* R = p.dLdrec_f + (active ? m * 3 * p.n_bins : 0);
+    const bool vec = (p.n_bins & 3) == 0;
     // the FP64 adjoint's bin coordinate of a sample, and its split into floor + fraction
     auto u_fp64 = [&](double t, double x, double y, double z) {
         return __dmul_rn(__dsub_rn(advanced_time_fp64(nx, ny, nz, x, y, z, t), p.t_min),
@@ -507,6 +508,12 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
         bool nzc = false;
         float4 pb = make_float4(0.f, 0.f, 0.f, 0.f), pa = pb;   // sample i-1
         int64_t J = 0;   // sample i-1 at J + f
+        // the pixel's record-gradient rows are read in increasing j: with n_bins a multiple
+        // of 4 (16-byte aligned rows) a lane keeps the 16-byte chunk of each row holding the
+        // current j, one vector load per row and 4 bins instead of one scalar per bin (the
+        // lanes of a warp read 32 different rows, so loads cost one L1 wavefront per lane)
+        int64_t jc = -4;
+        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0, c2 = c0;
         float f = 0.0f;
         for (int64_t i0 = 0; i0 < p.ns1; i0 += kAdjTile) {
             const int n = (int)min((int64_t)kAdjTile, p.ns1 - i0);
@@ -583,7 +590,23 @@ __global__ void __launch_bounds__(kAdjThreads) adj_deposit_mixed_kernel(AdjArgs 
                         for (int64_t j = ja; j <= jz; ++j) {
                             const float tj = (float)(j - Jf);
                             const float wa = (ua - tj) * iden, wb = (tj - ub) * iden;
-                            const float R0 = R[j], R1 = R[p.n_bins + j], R2 = R[2 * p.n_bins + j];
+                            float R0, R1, R2;
+                            if (vec) {   // 16-byte chunks of the three rows, reloaded per 4 bins
+                                if ((j & ~int64_t(3)) != jc) {
+                                    jc = j & ~int64_t(3);
+                                    c0 = __ldg(reinterpret_cast<const float4*>(R + jc));
+                                    c1 = __ldg(reinterpret_cast<const float4*>(R + p.n_bins + jc));
+                                    c2 = __ldg(reinterpret_cast<const float4*>(R + 2 * p.n_bins + jc));
+                                }
+                                const int e = (int)(j & 3);
+                                R0 = e == 0 ? c0.x : e == 1 ? c0.y : e == 2 ? c0.z : c0.w;
+                                R1 = e == 0 ? c1.x : e == 1 ? c1.y : e == 2 ? c1.z : c1.w;
+                                R2 = e == 0 ? c2.x : e == 1 ? c2.y : e == 2 ? c2.z : c2.w;
+                            } else {
+                                R0 = R[j];
+                                R1 = R[p.n_bins + j];
+                                R2 = R[2 * p.n_bins + j];
+                            }
                             Gc[0] = fmaf(R0, wa, Gc[0]);
                             Gc[1] = fmaf(R1, wa, Gc[1]);
                             Gc[2] = fmaf(R2, wa, Gc[2]);
