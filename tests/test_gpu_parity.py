@@ -315,3 +315,30 @@ def test_precision_bit_quiet_on_a_resolved_bunch():
         torch.cuda.synchronize()
         assert int(st.item()) & lw.LW_ST_PRECISION == 0
         assert float(torch.linalg.norm(S.double() - S64) / torch.linalg.norm(S64)) <= MIXED_TOL
+
+
+def test_precision_check_launch_leaves_the_record_complete():
+    """With a status word the deposit launches its precision check as a programmatic
+    dependent (it starts beside the deposit's last CTAs and ends only after the deposit
+    grid); a spectrum enqueued right after must see the finished record: records and
+    spectra equal those of a deposit without the check, up to the order of the FP32
+    reductions, on a case with enough electron chunks for the check's stride of 64."""
+    w = configs.c2_paper(n_e=400, n_s=2000, nx=32, n_bins=16384)
+    tr = w.traj
+    dev = torch.device("cuda")
+    traj = lw.lw_trajectories_upload(tr.t, tr.r, tr.beta, tr.beta_dot,
+                                     sections=lw.LW_SECTION_MIXED, device=dev)
+    det = lw.Detector(w.n_hat, device=dev)
+    b = lw.lw_grid_bounds(traj, det).cpu().numpy()
+    grid = lw.grid_from_bounds(b[0], b[1], w.n_bins)
+    P = lw.LW_MIXED_F32X4
+    rec_a = lw.lw_deposit_time_domain(traj, det, grid, P)
+    S_a = lw.lw_spectrum(rec_a, P, det.n_pix, grid)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rec_b = lw.lw_deposit_time_domain(traj, det, grid, P, status=status)
+    S_b = lw.lw_spectrum(rec_b, P, det.n_pix, grid)
+    torch.cuda.synchronize()
+    ra, rb = rec_a.double().cpu().numpy(), rec_b.double().cpu().numpy()
+    assert np.abs(ra).max() > 0
+    assert rel_l2(rb, ra) <= 1e-6
+    assert rel_l2(S_b.double().cpu().numpy(), S_a.double().cpu().numpy()) <= 1e-6
