@@ -71,9 +71,11 @@ TrajLayout make_layout(int64_t n_e, int64_t n_s, int t_per_e, int sections, int 
 // finite values, |beta| < 1 (evaluated as ((bx*bx + by*by) + bz*bz) < 1),
 // strictly increasing lab time, and with `check_steps` consecutive samples
 // closer than c0 dt (LW_ST_STEP otherwise) -- and, when `scan` is non-null, the mixed
-// section (block-relative float4, six field floats, per-block anchor).
-// The [sample][3] inputs and the [sample][6] field output are moved through
-// shared memory so that every global access is a contiguous run.
+// section (block-relative float4, the field records as a float4 and a float2, per-block
+// anchor).
+// The [sample][3] inputs are copied into shared memory (cp.async, the next electron's chunk
+// while this one is converted) so that every global load is a contiguous run; the outputs
+// are one float4 and one float2 store per sample.
 constexpr int kPrepThreads = 256;
 
 // isfinite on the exponent bits (integer pipe; the FP64 pipe is the upload's bound)
