@@ -157,6 +157,8 @@ struct AdjArgs {
     const double* dLdrec;   // [n_pix][3][n_bins]
     const float* dLdrec_f;  // mixed: dLdrec * 2^-e in FP32 (|values| < 2)
     const double* rscale;   // mixed: 2^e (device scalar)
+    float* f_grad;          // mixed: per sample 12 floats, (dL/du_a n, dL/dbeta, dL/dbdot, 0)
+                            // on the record gradient's scale, FP32 sums
     double* g_r;
     double* g_beta;
     double* g_bdot;
@@ -437,12 +439,30 @@ __device__ __forceinline__ void flush_sample_f32(const AdjArgs& p, bool act, con
     }
     for (int c = 0; c < 9; ++c)
         for (int s = 16; s > 0; s >>= 1) o[c] += __shfl_xor_sync(0xffffffffu, o[c], s);
-    if ((threadIdx.x & 31) == 0) {
-        const int64_t sidx = 3 * (k * p.ns1 + i);
+    if ((threadIdx.x & 31) == 0) {   // three 16-byte FP32 reductions (no FP64 in the loop)
+        float* f = p.f_grad + 12 * (k * p.ns1 + i);
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(f), "f"(o[0]),
+                     "f"(o[1]), "f"(o[2]), "f"(o[3]) : "memory");
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(f + 4), "f"(o[4]),
+                     "f"(o[5]), "f"(o[6]), "f"(o[7]) : "memory");
+        asm volatile("red.global.add.f32 [%0], %1;" ::"l"(f + 8), "f"(o[8]) : "memory");
+    }
+}
+
+// the FP32 sums in FP64, unscaled, added to the caller's gradients
+__global__ void adj_finish_kernel(const float* __restrict__ f, int64_t n_samples,
+                                  const double* __restrict__ rscale, double inv_dtu,
+                                  double* __restrict__ g_r, double* __restrict__ g_b,
+                                  double* __restrict__ g_a) {
+    const double r_scale = *rscale;
+    const double u_scale = -r_scale * inv_dtu * kInvC0;   // dL/dr = -(dL/du_a) n / (c0 dt_u)
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_samples;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const float* q = f + 12 * s;
         for (int c = 0; c < 3; ++c) {
-            atomicAdd(p.g_r + sidx + c, (double)o[c] * u_scale);
-            atomicAdd(p.g_beta + sidx + c, (double)o[3 + c] * r_scale);
-            atomicAdd(p.g_bdot + sidx + c, (double)o[6 + c] * r_scale);
+            g_r[3 * s + c] += (double)q[c] * u_scale;
+            g_b[3 * s + c] += (double)q[3 + c] * r_scale;
+            g_a[3 * s + c] += (double)q[6 + c] * r_scale;
         }
     }
 }
@@ -678,7 +698,8 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
     const size_t tw_bytes = align256(sizeof(double2) * (size_t)N);
     const size_t y_bytes = direct ? 0 : align256(sizeof(double2) * (size_t)(pairs * N));
     // mixed: the scaled FP32 record gradient, its largest magnitude and the scale
-    const size_t f_bytes = mixed ? align256(sizeof(float) * (size_t)(rows * N)) + 256 : 0;
+    const size_t gsum_bytes = mixed ? align256(sizeof(float) * 12 * (size_t)(traj->n_e * (traj->n_s + 1))) : 0;
+    const size_t f_bytes = mixed ? align256(sizeof(float) * (size_t)(rows * N)) + 256 + gsum_bytes : 0;
     const size_t need = rec_bytes + tw_bytes + y_bytes + f_bytes;
     if (!ws) {
         *ws_bytes = need;
@@ -773,6 +794,14 @@ extern "C" int lw_spectrum_grad(const lw_traj* traj, const lw_detector* det, con
     if (launch_status() != LW_OK) return LW_ECUDA;
     a.dLdrec_f = Rf;
     a.rscale = rscale;
+    a.f_grad = reinterpret_cast<float*>(fbase + align256(sizeof(float) * (size_t)(rows * N)) + 256);
+    const int64_t n_samples = traj->n_e * (traj->n_s + 1);
+    if (cudaMemsetAsync(a.f_grad, 0, sizeof(float) * 12 * (size_t)n_samples, st) != cudaSuccess)
+        return LW_ECUDA;
     adj_deposit_mixed_kernel<<<g, kAdjThreads, 0, st>>>(a);
+    if (launch_status() != LW_OK) return LW_ECUDA;
+    const int fg = (int)std::min<int64_t>((n_samples + 255) / 256, (int64_t)kSms * 8);
+    adj_finish_kernel<<<fg, 256, 0, st>>>(a.f_grad, n_samples, rscale, a.inv_dtu, a.g_r, a.g_beta,
+                                          a.g_bdot);
     return launch_status();
 }
