@@ -29,6 +29,21 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) {
     r.y = a.y - b.y;
     return r;
 }
+// (s.x^2 + d.x^2, s.y^2 + d.y^2)
+template <typename C> __device__ __forceinline__ C sumsq2(C s, C d) {
+    C r;
+    r.x = s.x * s.x + d.x * d.x;
+    r.y = s.y * s.y + d.y * d.y;
+    return r;
+}
+__device__ __forceinline__ float2 sumsq2(float2 s, float2 d) {
+    return __ffma2_rn(d, d, __fmul2_rn(s, s));
+}
+// FP32 pairs: one packed instruction each (a - b as the exact b * (-1) + a)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
 
 __device__ __forceinline__ unsigned bitrev(unsigned x, int bits) {
     return __brev(x) >> (32 - bits);

@@ -305,21 +305,31 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
         for (int kind = 0; kind < 3; ++kind) {
             const C zl = bz[ol + 2 * kind];
             const C zn = bm[om + 2 * kind];
-            C A, B;   // spectra of the two real rows of the sequence
-            A.x = (T)0.5 * (zl.x + zn.x);
-            A.y = (T)0.5 * (zl.y - zn.y);
-            B.x = (T)0.5 * (zl.y + zn.y);
-            B.y = (T)0.5 * (zn.x - zl.x);
-            const T pa = A.x * A.x + A.y * A.y;
-            const T pb = B.x * B.x + B.y * B.y;
+            // s = zl + zn, d = zl - zn: the two real rows' spectra are A = (s.x, d.y) / 2
+            // and B = (s.y, -d.x) / 2
+            const C sv = cadd(zl, zn), dv = csub(zl, zn);
+            C A, B;
+            A.x = (T)0.5 * sv.x;
+            A.y = (T)0.5 * dv.y;
+            B.x = (T)0.5 * sv.y;
+            B.y = (T)-0.5 * dv.x;
+            T pa, pb;   // (x, y) of one pixel: pa = |A|^2 + |B|^2; (z0, z1): |A|^2, |B|^2
+            if (kind < 2) {   // |A|^2 + |B|^2 = (|s|^2 + |d|^2) / 4
+                const C q = sumsq2(sv, dv);
+                pa = (T)0.25 * (q.x + q.y);
+                pb = (T)0;
+            } else {
+                pa = (T)0.25 * (sv.x * sv.x + dv.y * dv.y);
+                pb = (T)0.25 * (sv.y * sv.y + dv.x * dv.x);
+            }
             if (kind == 0) {          // (x0, y0)
-                pw0 += pa + pb;
+                pw0 += pa;
                 if (X) {
                     X[(m0 * 3 + 0) * nl + l] = A;
                     X[(m0 * 3 + 1) * nl + l] = B;
                 }
             } else if (kind == 1) {   // (x1, y1)
-                pw1 += pa + pb;
+                pw1 += pa;
                 if (X && has1) {
                     X[(m1 * 3 + 0) * nl + l] = A;
                     X[(m1 * 3 + 1) * nl + l] = B;
