@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
     // every element of the tile is copied straight into its bit-reversed slot by
     // cp.async, all of them in flight at once; rows past N1/2 are zero-filled. A thread
     // keeps its j2 values (TPC threads per column, CPI columns per round) so that the
-    // bit-reversed slot offsets are computed once; a round's column is decoded once.
+    // bit-reversed slot offsets are computed once. The rounds are unrolled: with one
+    // column per round (N2 >= kFftThreads) every column's side, kind and source row
+    // offset are constants of the code, and a copy is an address add and the copy.
     constexpr int TPC = N2 < kFftThreads ? N2 : kFftThreads;
     constexpr int CPI = kFftThreads / TPC;
     constexpr int JPT = N2 / TPC;
@@ -258,8 +260,11 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 4 : 2)
         const int jr = bitrev(threadIdx.x % TPC + u * TPC, logN2);
         jslot[u] = jr * Cn + (jr >> sh);
     }
-#pragma unroll 1
-    for (int col = threadIdx.x / TPC; col < Cn; col += CPI) {
+    const int col0 = CPI == 1 ? 0 : (int)threadIdx.x / TPC;
+#pragma unroll
+    for (int cc = 0; cc < (Cn + CPI - 1) / CPI; ++cc) {
+        const int col = cc * CPI + col0;
+        if (CPI > 1 && col >= Cn) break;
         const int side = col & 1, kind = (col >> 1) % 3, r = col / 6;
         const int l1 = r0 + r;
         const bool valid = l1 <= N1 / 2;
