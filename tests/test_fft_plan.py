@@ -3,7 +3,9 @@
 exp(2 pi i q0 rev_R(m) / (2^R h)) and then applies radix-2 stages with constant roots)
 equals numpy's transform with the + sign, for the pass plans the kernels use; and the
 padded layout's slot of element i0 + m h splits into a per-group base plus a per-m
-constant, which the compile-time passes rely on."""
+constant, which the compile-time passes rely on; and the four-step pass 2's per-thread
+index work (its unrolled tile copy and its output split into Z_l and Z_{N-l}) covers every
+slot and every spectrum bin exactly once."""
 import numpy as np
 import pytest
 
@@ -92,3 +94,95 @@ def test_padded_bit_reversed_stores_hit_distinct_banks():
                 slots = [_rev(t, logl) * cn + (_rev(t, logl) >> sh) for t in range(t0, t0 + 32)]
                 banks = [x % 16 for x in slots]
                 assert max(banks.count(b) for b in set(banks)) == 2
+
+
+# ---- four-step pass 2: the tile copy and the output split, modelled per thread
+
+def _pass2_rows(n2, logn2, elem_bytes):
+    """Rows per CTA as the host picks them: up to 4 within 96 KB of shared memory."""
+    rows = 4
+    while rows > 1 and elem_bytes * (n2 * 6 * rows + (n2 >> (logn2 - 5))) > 96 * 1024:
+        rows >>= 1
+    return rows
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("logn2", [6, 7, 8, 9])
+def test_pass2_copy_rounds_fill_every_slot_once(rows, logn2):
+    """The unrolled copy rounds (col = cc * CPI + col0, CPI columns per round, the last
+    round cut at Cn) put element j2 of every column into its bit-reversed padded slot
+    exactly once, from row `l1` (side 0) or `N1 - l1` (side 1) of sequence `kind`, and
+    zero-fill the columns of rows past N1 / 2."""
+    n2, cn, sh = 1 << logn2, 6 * rows, logn2 - 5
+    tpc = min(n2, THREADS)
+    cpi, jpt = THREADS // tpc, n2 // tpc
+    for logn1 in (logn2 - 1, logn2):
+        n1 = 1 << logn1
+        n = n1 * n2
+        groups = (n1 // 2 + 1 + rows - 1) // rows
+        for bx in sorted({0, 1, groups - 1}):
+            r0 = bx * rows
+            seen = {}
+            for t in range(THREADS):
+                col0 = 0 if cpi == 1 else t // tpc
+                for cc in range((cn + cpi - 1) // cpi):
+                    col = cc * cpi + col0
+                    if cpi > 1 and col >= cn:
+                        break
+                    side, kind, r = col & 1, (col >> 1) % 3, col // 6
+                    l1 = r0 + r
+                    valid = l1 <= n1 // 2
+                    row = ((n1 - l1) & (n1 - 1) if side else l1) if valid else 0
+                    for u in range(jpt):
+                        j = t % tpc + u * tpc
+                        jr = _rev(j, logn2)
+                        slot = jr * cn + (jr >> sh) + col
+                        assert slot not in seen
+                        seen[slot] = (kind * n + row * n2 + j, valid)
+            want = {_rev(j, logn2) * cn + (_rev(j, logn2) >> sh) + col: (j, col)
+                    for j in range(n2) for col in range(cn)}
+            assert set(seen) == set(want)
+            for slot, (j, col) in want.items():
+                side, kind, r = col & 1, (col >> 1) % 3, col // 6
+                l1 = r0 + r
+                src, valid = seen[slot]
+                assert valid == (l1 <= n1 // 2)
+                if valid:
+                    row = (n1 - l1) & (n1 - 1) if side else l1
+                    assert src == kind * n + row * n2 + j
+
+
+@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18])
+@pytest.mark.parametrize("elem_bytes", [8, 16])
+def test_pass2_writes_every_spectrum_bin_once_with_its_mirror(logn, elem_bytes):
+    """Over all CTAs of a pixel pair, the output stage writes every l = 0 .. N/2 exactly
+    once, as l = row + N1 l2 of the column it holds, and reads Z_{N-l} at row' + N1 l2m of
+    the other side's column (row' = the mirror row), i.e. row' + N1 l2m = N - l mod N."""
+    logn2 = (logn + 1) // 2
+    logn1 = logn - logn2
+    n1, n2, n = 1 << logn1, 1 << logn2, 1 << logn
+    rows = _pass2_rows(n2, logn2, elem_bytes)
+    groups = (n1 // 2 + 1 + rows - 1) // rows
+    l2step = THREADS // (2 * rows)
+    half = n // 2
+    count = np.zeros(half + 1, np.int64)
+    for bx in range(groups):
+        r0 = bx * rows
+        for t in range(THREADS):
+            r, side = t % rows, (t // rows) & 1
+            l1 = r0 + r
+            if l1 > n1 // 2:
+                continue
+            l1p = (n1 - l1) & (n1 - 1)
+            if side == 1 and l1p == l1:
+                continue
+            row = l1p if side else l1
+            other = l1 if side else l1p
+            for l2 in range(t // (2 * rows), n2, l2step):
+                l = row + n1 * l2
+                if l > half:
+                    break
+                l2m = (n2 - l2) & (n2 - 1) if row == 0 else n2 - 1 - l2
+                assert (other + n1 * l2m) % n == (n - l) % n
+                count[l] += 1
+    assert (count == 1).all()
