@@ -351,7 +351,7 @@ def run_ours(args, rank, world, dist):
     }
     # roofline of the dominant kernel (the mixed deposit): the work of one launch by the
     # model in deposit_work(), against pipe peaks measured on this GPU just before the
-    # timed region (HBM: the measured copy bandwidth)
+    # timed region (HBM: the copy bandwidth recorded in MEASURED_PEAKS.json)
     hbm_peak, peak_src = 6800.0, "fallback"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
