@@ -163,6 +163,31 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _dev(name, t, dtype=None, numel=0):
+    """Check a tensor that the library reads or writes as device memory: a contiguous CUDA
+    tensor (of ``dtype`` when given) of at least ``numel`` elements.  A host tensor or a
+    short buffer would reach a kernel as a bad device address, so it is refused here."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: {t.dtype} given, {dtype} required")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements given, at least {numel} required")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    return t
+
+
+def _ws(name, ws):
+    """A caller's workspace: device bytes starting on a 256-byte boundary."""
+    _dev(name, ws)
+    if ws.data_ptr() % 256:
+        raise ValueError(f"{name}: must start on a 256-byte boundary (see workspace())")
+    return ws
+
+
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
     """A 256-byte aligned device byte buffer (for the library's workspaces)."""
     return _aligned_bytes(nbytes, device)
@@ -209,6 +234,7 @@ class Detector:
         return self.n_hat.shape[0]
 
     def c(self) -> lw_detector:
+        _dev("Detector.n_hat", self.n_hat, torch.float64, 3 * self.n_pix)
         return lw_detector(self.n_pix, self.n_hat.data_ptr(), self.R)
 
 
@@ -291,26 +317,36 @@ def lw_trajectories_upload(t, r, beta, beta_dot, sections=LW_SECTION_FP64 | LW_S
 
 def lw_grid_bounds(traj: Trajectories, det: Detector, out=None):
     """Device double[2] = (t_u^min, t_u^max) of Eqs. (tu_min), (tu_max)."""
-    lib = load()
     if out is None:
         out = torch.empty(2, dtype=torch.float64, device=det.n_hat.device)
+    _dev("out", out, torch.float64, 2)
+    lib = load()
     d = det.c()
     _check("lw_grid_bounds", lib.lw_grid_bounds(ctypes.byref(traj.view), ctypes.byref(d),
                                                 _ptr(out), _stream()))
     return out
 
 
+def _record_layout(n_pix: int, n_bins: int, precision: int):
+    if precision in (LW_FP64, LW_MIXED):
+        return (n_pix, 3, n_bins), torch.float64
+    if precision == LW_MIXED_F32:
+        return (n_pix, 3, n_bins), torch.float32
+    if precision == LW_MIXED_F32X4:
+        return (n_pix, n_bins, 4), torch.float32
+    return (n_pix, 3, n_bins, 2), torch.float32
+
+
+def _record_arg(name, record, n_pix: int, n_bins: int, precision: int):
+    shape, dtype = _record_layout(n_pix, n_bins, precision)
+    return _dev(name, record, dtype, math.prod(shape))
+
+
 def record_shape(det: Detector, grid: Grid, precision: int):
     """(shape, dtype) of the record: FP64 and MIXED accumulate in float64,
     MIXED_KAHAN in (sum, compensation) float32 pairs, MIXED_F32 in float32,
     MIXED_F32X4 in float32 (x, y, z, 0) per pixel and grid point."""
-    if precision in (LW_FP64, LW_MIXED):
-        return (det.n_pix, 3, grid.n_bins), torch.float64
-    if precision == LW_MIXED_F32:
-        return (det.n_pix, 3, grid.n_bins), torch.float32
-    if precision == LW_MIXED_F32X4:
-        return (det.n_pix, grid.n_bins, 4), torch.float32
-    return (det.n_pix, 3, grid.n_bins, 2), torch.float32
+    return _record_layout(det.n_pix, grid.n_bins, precision)
 
 
 def record_value(record: torch.Tensor, precision: int) -> torch.Tensor:
@@ -326,12 +362,16 @@ def lw_deposit_time_domain(traj: Trajectories, det: Detector, grid: Grid, precis
                            field_flags: int = LW_FIELD_ACCEL, record=None, accumulate=False,
                            status=None):
     """Algorithm 2 for every pixel; returns the record (see record_shape)."""
-    lib = load()
     shape, dtype = record_shape(det, grid, precision)
     if record is None:
         record = torch.empty(shape, dtype=dtype, device=det.n_hat.device)
         accumulate = False
-    assert tuple(record.shape) == shape and record.dtype == dtype and record.is_contiguous()
+    if tuple(record.shape) != shape:
+        raise ValueError(f"record: shape {tuple(record.shape)} given, {shape} required")
+    _dev("record", record, dtype)
+    if status is not None:
+        _dev("status", status, torch.int32, 1)
+    lib = load()
     d = det.c()
     g = grid.c()
     _check("lw_deposit_time_domain",
@@ -353,10 +393,15 @@ def spectrum_workspace_bytes(precision: int, n_pix: int, grid: Grid) -> int:
 def lw_spectrum(record, precision: int, n_pix: int, grid: Grid, q: float = Q_E, want_X=False,
                 ws=None, out=None):
     """S [n_pix][n_bins/2+1] (FP64 or FP32) and optionally X' [n_pix][3][n_bins/2+1] complex."""
-    lib = load()
+    _record_arg("record", record, n_pix, grid.n_bins, precision)
     dev = record.device
     dtype = torch.float64 if precision == LW_FP64 else torch.float32
     nl = grid.n_bins // 2 + 1
+    if out is not None:
+        _dev("out", out, dtype, n_pix * nl)
+    if ws is not None:
+        _ws("ws", ws)
+    lib = load()
     S = out if out is not None else torch.empty((n_pix, nl), dtype=dtype, device=dev)
     X = torch.empty((n_pix, 3, nl, 2), dtype=dtype, device=dev) if want_X else None
     need = spectrum_workspace_bytes(precision, n_pix, grid)
@@ -380,7 +425,6 @@ def lw_spectrum_grad(traj: Trajectories, det: Detector, grid: Grid, X_save, dL_d
     precision defaults to LW_FP64 or LW_MIXED after X_save's type.  dL_dS: float64
     [n_pix][n_bins/2+1].  Returns (dL/dr, dL/dbeta, dL/dbeta_dot), each float64
     [n_e][n_s+1][3] (added to ``out`` when given)."""
-    lib = load()
     dev = det.n_hat.device
     shape = (traj.n_e, traj.n_s + 1, 3)
     if out is None:
@@ -388,8 +432,13 @@ def lw_spectrum_grad(traj: Trajectories, det: Detector, grid: Grid, X_save, dL_d
     X = torch.view_as_real(X_save.contiguous()) if X_save.is_complex() else X_save.contiguous()
     if precision is None:
         precision = LW_FP64 if X.dtype == torch.float64 else LW_MIXED
-    assert X.dtype == (torch.float64 if precision == LW_FP64 else torch.float32)
-    g = dL_dS.to(torch.float64).contiguous()
+    nl = grid.n_bins // 2 + 1
+    _dev("X_save", X, torch.float64 if precision == LW_FP64 else torch.float32,
+         det.n_pix * 3 * nl * 2)
+    g = _dev("dL_dS", dL_dS.to(torch.float64).contiguous(), numel=det.n_pix * nl)
+    for i, o in enumerate(out):
+        _dev(f"out[{i}]", o, torch.float64, math.prod(shape))
+    lib = load()
     d = det.c()
     gr = grid.c()
     nbytes = ctypes.c_size_t(0)
@@ -419,8 +468,12 @@ class BatchPlan:
 def lw_batch_plan(trajs, dets, grids, records, precision=LW_MIXED, field_flags=LW_FIELD_ACCEL,
                   statuses=None, e_chunks=None) -> BatchPlan:
     """Plan one persistent launch over several variants (lists of equal length)."""
-    lib = load()
     n = len(trajs)
+    for v in range(n):
+        _record_arg(f"records[{v}]", records[v], dets[v].n_pix, grids[v].n_bins, precision)
+        if statuses is not None:
+            _dev(f"statuses[{v}]", statuses[v], torch.int32, 1)
+    lib = load()
     items = (lw_batch_item * n)()
     dets_c = [d.c() for d in dets]
     for v in range(n):
@@ -452,9 +505,10 @@ def lw_spectrum_fdm(traj: Trajectories, det: Detector, omega0: float, d_omega: f
                     n_omega: int, dt: float, q: float = Q_E, out=None):
     """Frequency-domain method (Eq. inty_dft) on omega_w = omega0 + w d_omega; float64
     [n_pix][n_omega]."""
-    lib = load()
     S = out if out is not None else torch.empty((det.n_pix, int(n_omega)), dtype=torch.float64,
                                                 device=det.n_hat.device)
+    _dev("out", S, torch.float64, det.n_pix * int(n_omega))
+    lib = load()
     d = det.c()
     _check("lw_spectrum_fdm", lib.lw_spectrum_fdm(ctypes.byref(traj.view), ctypes.byref(d),
                                                   float(omega0), float(d_omega), int(n_omega),
@@ -471,6 +525,12 @@ def lw_boris_push(r, u, t0: float, dt: float, n_steps: int, laser, t_out, r_out,
     Gaussian laser (lam, a0, w0, fwhm) and write the n_steps+1 samples into the outputs
     (t_out [n_steps+1], r_out/beta_out/bdot_out [n_e, n_steps+1, 3]); sample s is at time
     t0 + dt (step0 + s)."""
+    n_e = r.shape[0]
+    _dev("r", r, torch.float64, 3 * n_e)
+    _dev("u", u, torch.float64, 3 * n_e)
+    _dev("t_out", t_out, torch.float64, int(n_steps) + 1)
+    for name, o in (("r_out", r_out), ("beta_out", beta_out), ("bdot_out", bdot_out)):
+        _dev(name, o, torch.float64, 3 * n_e * (int(n_steps) + 1))
     lib = load()
     L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
     _check("lw_boris_push", lib.lw_boris_push(_ptr(r), _ptr(u), r.shape[0], float(t0),
@@ -486,13 +546,20 @@ def lw_boris_push_grad(r0, u0, t0: float, dt: float, n_steps: int, laser, dL_dr,
     """Gradient through lw_boris_push from (r0, u0) (float64 CUDA tensors [n_e, 3], read
     only) over n_steps steps: given dL/d(r, beta, beta_dot) [n_e, n_steps+1, 3], returns
     (dL/du0 [n_e, 3], dL/d(a0, w0) [2]) (added to ``out`` when given)."""
-    lib = load()
     dev = u0.device
+    n_e = u0.shape[0]
     if out is None:
         out = (torch.zeros_like(u0, dtype=torch.float64),
                torch.zeros(2, dtype=torch.float64, device=dev))
-    L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
+    _dev("r0", r0.contiguous(), torch.float64, 3 * n_e)
+    _dev("u0", u0.contiguous(), torch.float64, 3 * n_e)
     gr, gb, ga = (x.contiguous() for x in (dL_dr, dL_dbeta, dL_dbeta_dot))
+    for name, x in (("dL_dr", gr), ("dL_dbeta", gb), ("dL_dbeta_dot", ga)):
+        _dev(name, x, torch.float64, 3 * n_e * (int(n_steps) + 1))
+    _dev("out[0]", out[0], torch.float64, 3 * n_e)
+    _dev("out[1]", out[1], torch.float64, 2)
+    lib = load()
+    L = lw_laser(float(laser[0]), float(laser[1]), float(laser[2]), float(laser[3]))
     _check("lw_boris_push_grad",
            lib.lw_boris_push_grad(_ptr(r0.contiguous()), _ptr(u0.contiguous()), u0.shape[0],
                                   float(t0), float(dt), int(n_steps), ctypes.byref(L),
@@ -506,10 +573,13 @@ def lw_spectrum_static(record, precision: int, n_pix: int, grid: Grid, q: float 
     """lw_spectrum without a workspace argument: the library's fixed device scratch
     array is used instead (see include/lw.h); nothing is allocated by the library.
     Output tensors are allocated here unless passed in."""
-    lib = load()
+    _record_arg("record", record, n_pix, grid.n_bins, precision)
     dev = record.device
     dtype = torch.float64 if precision == LW_FP64 else torch.float32
     nl = grid.n_bins // 2 + 1
+    if out is not None:
+        _dev("out", out, dtype, n_pix * nl)
+    lib = load()
     S = out if out is not None else torch.empty((n_pix, nl), dtype=dtype, device=dev)
     X = torch.empty((n_pix, 3, nl, 2), dtype=dtype, device=dev) if want_X else None
     g = grid.c()
