@@ -142,3 +142,60 @@ def test_enum_values_match_the_header(tmp_path):
                    check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert [int(x) for x in out] == [getattr(lw, n) for n in names]
+
+
+def test_pusher_adjoint_fdm_and_batch_argument_checks(lib):
+    """Every call below has an argument that the entry point refuses before any CUDA call
+    (the fake addresses are never dereferenced)."""
+    fake = ctypes.c_void_p(0x1000)
+    L = lw.lw_laser(0.8e-6, 0.5, 20e-6, 30e-15)
+    bad_L = lw.lw_laser(0.0, 0.5, 20e-6, 30e-15)
+    push = lambda r, n_e, dt, n_steps, laser, mass=9.1e-31: lib.lw_boris_push(  # noqa: E731
+        r, fake, n_e, 0.0, dt, 0, n_steps, ctypes.byref(laser), -1.6e-19, mass,
+        fake, fake, fake, fake, None)
+    assert push(None, 4, 1e-17, 10, L) == lw.LW_EINVAL           # no state
+    assert push(fake, 0, 1e-17, 10, L) == lw.LW_EINVAL           # no electrons
+    assert push(fake, 4, 0.0, 10, L) == lw.LW_EINVAL             # dt = 0
+    assert push(fake, 4, 1e-17, 0, L) == lw.LW_EINVAL            # no steps
+    assert push(fake, 4, 1e-17, 10, bad_L) == lw.LW_EINVAL       # wavelength 0
+    assert push(fake, 4, 1e-17, 10, L, mass=0.0) == lw.LW_EINVAL
+    grad = lambda n_e, n_steps, out: lib.lw_boris_push_grad(  # noqa: E731
+        fake, fake, n_e, 0.0, 1e-17, n_steps, ctypes.byref(L), -1.6e-19, 9.1e-31,
+        fake, fake, fake, out, fake, None)
+    assert grad(4, 10, None) == lw.LW_EINVAL
+    assert grad(0, 10, fake) == lw.LW_EINVAL
+    assert grad(4, 0, fake) == lw.LW_EINVAL
+
+    det = lw.lw_detector(4, 0x1000, 1.0)
+    view = lw.lw_traj()
+    view.n_e, view.n_s = 2, 10
+    view.sections = lw.LW_SECTION_MIXED                         # no FP64 section
+    assert lib.lw_spectrum_fdm(ctypes.byref(view), ctypes.byref(det), 1e15, 1e13, 16, 1e-17,
+                               1.6e-19, fake, None) == lw.LW_EINVAL
+    view.sections = lw.LW_SECTION_FP64
+    view.t, view.r = 0x1000, 0x1000
+    assert lib.lw_spectrum_fdm(ctypes.byref(view), ctypes.byref(det), 1e15, 1e13, 0, 1e-17,
+                               1.6e-19, fake, None) == lw.LW_EINVAL   # no frequencies
+    assert lib.lw_spectrum_fdm(ctypes.byref(view), ctypes.byref(det), 1e15, 1e13, 16, 0.0,
+                               1.6e-19, fake, None) == lw.LW_EINVAL   # dt = 0
+
+    nbytes = ctypes.c_size_t(0)
+    sg = lambda prec, flags, g: lib.lw_spectrum_grad(  # noqa: E731
+        ctypes.byref(view), ctypes.byref(det), ctypes.byref(g), prec, flags, None, None,
+        1.6e-19, None, None, None, None, ctypes.byref(nbytes), None)
+    ok_grid = lw.lw_grid(0.0, 1e-18, 256)
+    assert sg(7, lw.LW_FIELD_ACCEL, ok_grid) == lw.LW_EUNSUPPORTED          # unknown mode
+    assert sg(lw.LW_FP64, lw.LW_FIELD_VELOCITY, ok_grid) == lw.LW_EUNSUPPORTED
+    assert sg(lw.LW_FP64, lw.LW_FIELD_ACCEL, lw.lw_grid(0.0, 1e-18, 1000)) == \
+        lw.LW_EUNSUPPORTED                                                  # not 2^k
+    assert sg(lw.LW_FP64, lw.LW_FIELD_ACCEL, lw.lw_grid(0.0, 0.0, 256)) == lw.LW_EINVAL
+
+    plan = lw.lw_batch()
+    items = (lw.lw_batch_item * 1)()
+    assert lib.lw_batch_plan(None, 1, lw.LW_MIXED, 1, None, ctypes.byref(nbytes),
+                             ctypes.byref(plan), None) == lw.LW_EINVAL
+    assert lib.lw_batch_plan(items, 1, lw.LW_FP64, 1, None, ctypes.byref(nbytes),
+                             ctypes.byref(plan), None) == lw.LW_EUNSUPPORTED  # mixed only
+    assert lib.lw_batch_plan(items, 1, lw.LW_MIXED, 0, None, ctypes.byref(nbytes),
+                             ctypes.byref(plan), None) == lw.LW_EINVAL        # no field term
+    assert lib.lw_batch_deposit(ctypes.byref(lw.lw_batch()), None) == lw.LW_EINVAL
